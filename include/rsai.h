@@ -1,0 +1,245 @@
+/*
+ * rsai.h -- C ABI of the GB300 RSAI(tol) library (librsai.so).
+ *
+ * RSAI(tol) (Jia & Kang, residual based sparse approximate inverse) builds a
+ * sparse M ~ A^{-1} by minimising ||AM - I||_F (Section 2, Eq. 2.1) one column
+ * at a time (Eq. 2.2): for each k it solves the small least-squares problem
+ * min ||A(I_k,J_k) m - e_k(I_k)|| (Eq. 2.3) by Householder QR, forms the
+ * residual r_k = A m_k - e_k (Eq. 2.4), picks the c largest |r_k(i)| not used
+ * before (Algorithm 1 step 4, Eq. 3.2), adds the columns of those rows of A to
+ * J_k (step 5), drops entries |m_jk| <= tol_k (Eq. 4.3) and loops until
+ * ||r_k|| <= eps or l_max loops (step 3).
+ *
+ * Conventions for every entry point:
+ *   - Indices are 0-based, int32 for row/column indices, int64 for pointers
+ *     and counts.  CSR rows and CSC columns are strictly ascending; explicit
+ *     zeros count as structural nonzeros.
+ *   - Unless a comment says otherwise, pointers may be host or device memory
+ *     (the library asks the CUDA driver which one it is).  Host inputs are
+ *     copied to the device inside the call; host outputs are written back
+ *     before the call returns.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Work is stream-ordered: device inputs must stay valid until
+ *     the stream reaches the call, device outputs are valid once it has.
+ *   - Inputs are borrowed for the duration of the call.  A handle owns its
+ *     device memory until rsai_handle_free.
+ *   - Every function returns an rsai_status; no exception, device trap or
+ *     device assert ever crosses this boundary.  On error nothing is written
+ *     to outputs and *out handles are set to NULL.
+ *   - One GPU: the device current on the calling thread is used.
+ */
+#ifndef RSAI_H
+#define RSAI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RSAI_ABI_VERSION 1
+
+typedef enum {
+    RSAI_OK = 0,
+    RSAI_ERR_INVALID_ARG = 1,   /* NULL pointer, bad parameter value */
+    RSAI_ERR_SHAPE = 2,         /* n/nnz inconsistent between CSR and CSC */
+    RSAI_ERR_UNSORTED = 3,      /* indices not strictly ascending in a row/column */
+    RSAI_ERR_INDEX_RANGE = 4,   /* an index outside [0, n) or a bad pointer array */
+    RSAI_ERR_EMPTY_COLUMN = 5,  /* a column of A without nonzeros: A is singular */
+    RSAI_ERR_OOM = 6,           /* device allocation failed */
+    RSAI_ERR_CUDA = 7,          /* a CUDA runtime call failed */
+    RSAI_ERR_TIMEOUT = 8,       /* a bounded device wait ran out */
+    RSAI_ERR_WORKSPACE = 9,     /* a column outgrew every size bin (see rsai_stats) */
+    RSAI_ERR_BREAKDOWN = 10,    /* BiCGStab breakdown (rho = 0 or omega = 0) */
+    RSAI_ERR_NOT_CONVERGED = 11,/* BiCGStab reached maxit */
+    RSAI_ERR_NO_DEVICE = 12     /* no CUDA device is visible */
+} rsai_status;
+
+/* Sparse A in CSR (row_ptr[n+1], col_idx[nnz], val[nnz]). */
+typedef struct {
+    int64_t n, nnz;
+    const int64_t *row_ptr;
+    const int32_t *col_idx;
+    const double *val;
+} rsai_csr;
+
+/* The same A in CSC (col_ptr[n+1], row_idx[nnz], val[nnz]); used to gather
+ * the columns A(:,J_k) and their nonzero rows I_k (Section 2). */
+typedef struct {
+    int64_t n, nnz;
+    const int64_t *col_ptr;
+    const int32_t *row_idx;
+    const double *val;
+} rsai_csc;
+
+/* Dropping rule applied after every LS solve (Eq. 4.3 and its readings). */
+enum {
+    RSAI_DROP_NONE = 0,     /* basic RSAI, Algorithm 1 */
+    RSAI_DROP_ADAPTIVE = 1, /* tol_k = eps / (nnz(m_k) ||A||_1), Eq. 4.3 */
+    RSAI_DROP_FIXED = 2     /* tol_k = tol / ||A||_1 (absolute tol on A/||A||_1) */
+};
+
+/* Arithmetic of the LS solves.  The residual r_k, its norm, the dominant-row
+ * choice and the stopping test are FP64 in both. */
+enum {
+    RSAI_FP64 = 0,        /* Householder QR and solve in FP64 */
+    RSAI_FP32_REFINE = 1  /* QR in FP32, FP64 residual, one FP64 refinement step */
+};
+
+/* Flags */
+enum {
+    RSAI_FLAG_CHECKED = 1u /* extra device-side bounds checks (status, never a trap) */
+};
+
+/* Parameters of RSAI(tol) (Algorithm 1 step 1; Section 3 defaults c ~ 3,
+ * eps = 0.1..0.4, l_max ~ 10; Eq. 4.3). */
+typedef struct {
+    int32_t c;          /* dominant rows per loop (|Rhat_k|), 1..32 */
+    int32_t l_max;      /* maximum number of loops, >= 0 */
+    double eps;         /* stop when ||r_k|| <= eps, > 0 */
+    int32_t drop_mode;  /* RSAI_DROP_* */
+    double tol;         /* threshold of RSAI_DROP_FIXED, >= 0 */
+    int32_t precision;  /* RSAI_FP64 or RSAI_FP32_REFINE */
+    double tie_band;    /* relative tie band for the dominant-row order, >= 0 (default 1e-12) */
+    uint32_t flags;     /* RSAI_FLAG_* */
+} rsai_params;
+
+/* Per-build statistics (Section 5 reporting: spar = nnz(M)/nnz(A), n_c). */
+typedef struct {
+    int64_t n;            /* columns of M */
+    int64_t nnz_A;
+    int64_t nnz_M;        /* nonzeros of M */
+    int64_t n_c;          /* columns with ||r_k|| > eps (Section 5, n_c) */
+    double frob;          /* ||AM - I||_F = sqrt(sum_k ||r_k||^2) */
+    double norm1_A;       /* ||A||_1 (Eq. 4.3) */
+    double qr_flops;      /* algorithmic QR + solve flops (paper's QR update) */
+    double res_flops;     /* algorithmic FP64 residual flops */
+    double refine_flops;  /* FP32_REFINE only: algorithmic refinement flops */
+    double bytes;         /* algorithmic bytes */
+    int64_t loops;        /* sum over columns of the loops used */
+    int64_t solves;       /* LS solves */
+    int64_t drops;        /* solves that dropped entries (each costs a re-solve) */
+    int32_t p_max, q_max; /* largest LS problem met */
+    int64_t cols_bin[3];  /* columns finished by the warp, CTA and global bins */
+    int64_t n_rank;       /* columns flagged rank deficient */
+    int64_t n_nonfinite;  /* columns with a non-finite value */
+    int64_t n_failed;     /* columns no bin could hold (then status WORKSPACE) */
+} rsai_stats;
+
+/* Per-column outcome bits (rsai_get_columns). */
+enum { RSAI_COL_CONVERGED = 1, RSAI_COL_RANK = 2, RSAI_COL_NONFINITE = 4, RSAI_COL_FAILED = 8 };
+
+typedef struct rsai_handle rsai_handle;
+
+/* Library version (RSAI_ABI_VERSION). */
+int32_t rsai_abi_version(void);
+
+/* Text of a status code (static storage, never NULL). */
+const char *rsai_status_string(rsai_status s);
+
+/* Defaults of Section 3 / Section 5: c = 3, l_max = 10, eps = 0.3,
+ * RSAI_DROP_FIXED with tol = 1e-3, RSAI_FP64, tie_band = 1e-12. */
+rsai_status rsai_params_default(rsai_params *p);
+
+/* Host-only validation of a parameter block (no device work). */
+rsai_status rsai_params_check(const rsai_params *p);
+
+/*
+ * rsai_build -- build M column by column (Algorithm 1 + Eq. 4.3; the columns
+ * are independent, Eq. 2.2).
+ *   A, Acsc : the same n x n matrix in CSR and CSC (host or device arrays).
+ *   params   : see rsai_params.
+ *   out      : receives a handle owning M (CSR and CSC on the device), the
+ *              frozen pattern, ||r_k|| and the per-column flags.
+ * Validates A (shape, sorted, index range, no empty column) on the device
+ * before building.  The call returns when M and its statistics are ready.
+ * Errors: INVALID_ARG, SHAPE, UNSORTED, INDEX_RANGE, EMPTY_COLUMN, OOM, CUDA,
+ * WORKSPACE (a column outgrew every bin: the handle is still returned with
+ * those columns flagged RSAI_COL_FAILED).
+ */
+rsai_status rsai_build(const rsai_csr *A, const rsai_csc *Acsc, const rsai_params *params,
+                       void *stream, rsai_handle **out);
+
+/*
+ * rsai_rebuild -- run the build again on the handle's own copy of A after
+ * new values were written with rsai_set_values (same structure), reusing every
+ * buffer: no allocation, no host synchronisation; the launch sequence is
+ * recorded in a CUDA graph on first use and replayed afterwards.
+ * Statistics are refreshed by rsai_get_stats.  Errors: INVALID_ARG, CUDA.
+ */
+rsai_status rsai_rebuild(rsai_handle *h, void *stream);
+
+/* Overwrite the handle's copy of A's values (CSR order; host or device). */
+rsai_status rsai_set_values(rsai_handle *h, const double *A_val, void *stream);
+
+/* Statistics of the last build (synchronises the stream). */
+rsai_status rsai_get_stats(rsai_handle *h, void *stream, rsai_stats *out);
+
+/*
+ * rsai_get_M -- copy M out in CSR: row_ptr[n+1] (int64), col_idx[nnz_M]
+ * (int32), val[nnz_M]; any pointer may be NULL to skip it.  Sized by
+ * rsai_stats.nnz_M.  Host or device destinations.
+ */
+rsai_status rsai_get_M(rsai_handle *h, int64_t *row_ptr, int32_t *col_idx, double *val, void *stream);
+
+/* Per-column results: rho[k] = ||r_k||, loops[k], flags[k] (RSAI_COL_*);
+ * NULL pointers are skipped.  Host or device destinations. */
+rsai_status rsai_get_columns(rsai_handle *h, double *rho, int32_t *loops, int32_t *flags, void *stream);
+
+/*
+ * rsai_refit -- re-solve every column on the frozen pattern of M with new
+ * values of A (same structure, CSR order): m_k = argmin ||A(:,J_k) x - e_k||
+ * (Eq. 2.3), rho2[k] = ||r_k||^2 (Eq. 2.4).  No dropping, no pattern change.
+ * M_val receives the values in M's CSR order; either output may be NULL.
+ * Uses the handle's precision.  Device pointers only.
+ */
+rsai_status rsai_refit(rsai_handle *h, const double *A_val, double *M_val, double *rho2, void *stream);
+
+/*
+ * rsai_apply -- y = M x (the right preconditioner, Eq. 1.2: x = M y).
+ * x, y: device arrays of length n.
+ */
+rsai_status rsai_apply(rsai_handle *h, const double *x, double *y, void *stream);
+
+/*
+ * rsai_backward -- adjoint of the frozen-pattern solves.  For a scalar loss
+ * L(M, rho^2) with G_M = dL/dM (values in M's CSR order) and g = dL/d(rho_k^2)
+ * (may be NULL), writes dL/d(values of A) (CSR order of A) through every
+ * column's LS solve (Eq. 2.3) at the values A_val:
+ *   dL/dB_k = -r_k z_k^T - (B_k z_k) x_k^T + 2 g_k r_k x_k^T,
+ *   z_k = (B_k^T B_k)^{-1} G_M(J_k, k),  B_k = A(I_k, J_k),  x_k = m_k(J_k),
+ * each QR recomputed (not stored).  The pattern is not differentiated.
+ * Device pointers only.  The sum over columns has a fixed order.
+ */
+rsai_status rsai_backward(rsai_handle *h, const double *A_val, const double *grad_M, const double *grad_rho2,
+                          double *grad_A, void *stream);
+
+/*
+ * rsai_bicgstab -- right-preconditioned BiCGStab on A M y = b, x = M y
+ * (Eq. 1.2; Section 5 protocol: x0 = 0, stop when the recursive residual
+ * satisfies ||r||/||b|| < rtol at a half or full step, at most maxit
+ * iterations).  M may be NULL (no preconditioner).  A: device CSR (the
+ * handle's copy is not used, so A may differ from the matrix M was built for).
+ * b, x: device arrays.  On return *iters holds the iterations (a half-step exit
+ * counts as its full iteration) and *relres the true ||b - A x|| / ||b||.
+ * Errors: BREAKDOWN, NOT_CONVERGED (x still holds the last iterate).
+ */
+rsai_status rsai_bicgstab(const rsai_csr *A, rsai_handle *M, const double *b, double *x, double rtol,
+                          int32_t maxit, int32_t *iters, double *relres, void *stream);
+
+/* Release a handle and its device memory (NULL is a no-op). */
+void rsai_handle_free(rsai_handle *h);
+
+/*
+ * rsai_peak_fma -- measure the CUDA-core FMA pipe rate: launches a grid of
+ * independent FMA chains (FP32 if fp64 == 0, FP64 otherwise) and returns the
+ * achieved flop/s in *flops_per_s (2 flops per FMA).  Used for the roofline
+ * of the build kernels.
+ */
+rsai_status rsai_peak_fma(int32_t fp64, void *stream, double *flops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSAI_H */
