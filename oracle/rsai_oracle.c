@@ -51,7 +51,7 @@
  *     4 (p-p0) sum_{j<p0} (q0-j)  +  sum_{j=p0}^{p-1} (q-j) (2 + 4 (p-j))  +  p^2
  *   a solve after a drop, and the first solve, use p0 = 0 (no previous factor);
  *   residual: 2 nnz(A(:,J)) + 2 |S|.
- *   bytes: 12 nnz(A(:,j)) + 16 for every column j that ever enters J,
+ *   bytes: 12 nnz(A(:,j)) + 16 each time a column j enters J,
  *          4 nnz(A(i,:)) + 16 for every dominant row i, 36 per emitted entry
  *          (12 to emit it, 24 to move it once more into CSR).
  */
@@ -292,8 +292,6 @@ static void rsai_column(const omat *A, const oparams *P, int64_t k, ocol *out, o
     int32_t *J = malloc(sizeof(int32_t) * capJ);
     int32_t *Rset = malloc(sizeof(int32_t) * capR);
     double *m = malloc(sizeof(double) * capJ);
-    int32_t *seen_list = malloc(sizeof(int32_t) * 16);
-    int64_t cap_seen = 16, nseen = 0;
     int p = 1, nR = 0, l = 0, rank = 0, solves = 0, drops = 0;
     int64_t q = 0, q0 = 0;
     int p0 = 0, pmax = 1;
@@ -301,19 +299,8 @@ static void rsai_column(const omat *A, const oparams *P, int64_t k, ocol *out, o
     double qr_flops = 0.0, res_flops = 0.0, bytes = 0.0, rho = 0.0, nnzJ = 0.0;
     J[0] = (int32_t)k;
 
-    /* count the bytes of a column of A the first time it enters J */
-#define NOTE_COLUMN(j)                                                                  \
-    do {                                                                                \
-        int32_t jj_ = (j);                                                              \
-        if (find(seen_list, nseen, jj_) < 0) {                                          \
-            seen_list = grow(seen_list, &cap_seen, nseen + 1, sizeof(int32_t));          \
-            int64_t at_ = nseen;                                                        \
-            while (at_ > 0 && seen_list[at_ - 1] > jj_) { seen_list[at_] = seen_list[at_ - 1]; --at_; } \
-            seen_list[at_] = jj_;                                                       \
-            ++nseen;                                                                    \
-            bytes += 12.0 * (double)(A->col_ptr[jj_ + 1] - A->col_ptr[jj_]) + 16.0;       \
-        }                                                                               \
-    } while (0)
+    /* bytes of a column of A each time it enters J */
+#define NOTE_COLUMN(j) (bytes += 12.0 * (double)(A->col_ptr[(j) + 1] - A->col_ptr[(j)]) + 16.0)
 
     /* Solve on J, counting work; appended = 1 if J extends the last solved J. */
 #define SOLVE(appended)                                                              \
@@ -435,7 +422,6 @@ static void rsai_column(const omat *A, const oparams *P, int64_t k, ocol *out, o
     out->res_flops = res_flops;
     out->bytes = bytes;
     free(Rset);
-    free(seen_list);
     (void)n;
 }
 

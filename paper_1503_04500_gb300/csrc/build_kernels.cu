@@ -1,0 +1,405 @@
+// build_kernels.cu -- the RSAI(tol) build on the GPU: input checks, ||A||_1,
+// the three size bins of the column algorithm, and the assembly of M.
+//
+// Bins (one persistent launch each, columns pulled from an atomic queue; the
+// columns are independent, Section 2 Eq. 2.2):
+//   W  one warp per column, workspace in shared memory (small LS problems,
+//      e.g. stencil matrices: |I| <= 64, |J| <= 32)
+//   C  one CTA per column, workspace in shared memory (up to ~200 KB)
+//   G  one CTA per column, workspace in a global-memory slab per CTA (the
+//      long tail of matrices with dense rows, Section 4 "row irregular")
+// A column that outgrows a bin is pushed to the next bin's queue and
+// restarted there from J = {k}; the result is the same column of M.
+#include "kernels.h"
+
+namespace rsai {
+
+// ---------------------------------------------------------------------------
+// input checks (status codes, never a trap)
+
+__global__ void k_check_ptr(const int64_t *ptr, int64_t n, int64_t nnz, int32_t *err) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i > n) return;
+    if (i == 0 && ptr[0] != 0) set_error(err, RSAI_ERR_INDEX_RANGE);
+    if (i == n && ptr[n] != nnz) set_error(err, RSAI_ERR_SHAPE);
+    if (i < n && ptr[i] > ptr[i + 1]) set_error(err, RSAI_ERR_INDEX_RANGE);
+}
+
+__global__ void k_check_idx(const int64_t *ptr, const int32_t *idx, int64_t n, int32_t *err, int empty_is_error) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t a = ptr[i], b = ptr[i + 1];
+    if (empty_is_error && a == b) set_error(err, RSAI_ERR_EMPTY_COLUMN);
+    for (int64_t e = a; e < b; ++e) {
+        int32_t v = idx[e];
+        if (v < 0 || v >= n) { set_error(err, RSAI_ERR_INDEX_RANGE); return; }
+        if (e > a && idx[e - 1] >= v) { set_error(err, RSAI_ERR_UNSORTED); return; }
+    }
+}
+
+// CSR position of every CSC entry; checks that both describe the same matrix
+__global__ void k_csc_map(DevA A, int64_t *csc_to_csr, int32_t *err) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= A.n) return;
+    for (int64_t e = A.col_ptr[j]; e < A.col_ptr[j + 1]; ++e) {
+        int32_t i = A.row_idx[e];
+        int64_t lo = A.row_ptr[i];
+        int len = (int)(A.row_ptr[i + 1] - lo);
+        int pos = find_i32(A.col_idx + lo, len, (int32_t)j);
+        if (pos < 0 || A.val[lo + pos] != A.cval[e]) {
+            set_error(err, RSAI_ERR_SHAPE);
+            csc_to_csr[e] = -1;
+        } else {
+            csc_to_csr[e] = lo + pos;
+        }
+    }
+}
+
+// CSC values from CSR values through the map (after new values arrive)
+__global__ void k_csc_from_csr(const double *csr_val, const int64_t *csc_to_csr, double *cval, int64_t nnz) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < nnz) cval[e] = csr_val[csc_to_csr[e]];
+}
+
+// ||A||_1 = max_j sum_i |a_ij| (Eq. 4.3); nonnegative doubles order like their bits
+__global__ void k_norm1(const int64_t *col_ptr, const double *cval, int64_t n, double *out) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (j < n)
+        for (int64_t e = col_ptr[j]; e < col_ptr[j + 1]; ++e) s += fabs(cval[e]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax((unsigned long long *)out, (unsigned long long)__double_as_longlong(s));
+}
+
+// ---------------------------------------------------------------------------
+// the bins
+
+template <class Team, typename T>
+__device__ void emit_or_forward(const Team &team, Column<Team, T> &col, int st, const ColQueue &Q,
+                                const ColOut &O, bool last_bin, int bin) {
+    const int me = team.rank();
+    const int32_t k = col.k;
+    Work<T> &w = col.w;
+    if (st == COL_OVERFLOW) {
+        if (!last_bin) {
+            if (me == 0) {
+                uint32_t pos = atomicAdd(Q.ovf_count, 1u);
+                if ((int64_t)pos < Q.ovf_cap) Q.ovf_cols[pos] = k;
+                else set_error(O.err, RSAI_ERR_WORKSPACE);
+            }
+        } else if (me == 0) {
+            O.col_off[k] = 0;
+            O.col_len[k] = 0;
+            O.rho[k] = NAN;
+            O.loops[k] = 0;
+            O.flags[k] = RSAI_COL_FAILED;
+            w.ctr[CTR_FAILED] += 1.0;
+            set_error(O.err, RSAI_ERR_WORKSPACE);
+        }
+        team.sync();
+        return;
+    }
+    const int p = col.p;
+    unsigned long long off = 0;
+    if (me == 0) off = atomicAdd(O.pool_top, (unsigned long long)p);
+    off = team.bcast(off, 0);
+    if ((int64_t)(off + p) > O.pool_cap) {
+        if (me == 0) {
+            O.col_off[k] = 0;
+            O.col_len[k] = 0;
+            O.rho[k] = NAN;
+            O.flags[k] = RSAI_COL_FAILED;
+            w.ctr[CTR_FAILED] += 1.0;
+            set_error(O.err, RSAI_ERR_WORKSPACE);
+        }
+        team.sync();
+        return;
+    }
+    int fin = 1;
+    for (int c = me; c < p; c += Team::SIZE) {
+        O.pool_rows[off + c] = w.J[c];
+        O.pool_vals[off + c] = w.m[c];
+        fin &= isfinite(w.m[c]) ? 1 : 0;
+    }
+    fin = (int)team.sum((double)(1 - fin)) == 0 && isfinite(col.rho);
+    if (me == 0) {
+        int flags = (col.rho <= col.P.eps ? RSAI_COL_CONVERGED : 0) | (col.rank_flag ? RSAI_COL_RANK : 0) |
+                    (fin ? 0 : RSAI_COL_NONFINITE);
+        O.col_off[k] = (int64_t)off;
+        O.col_len[k] = p;
+        O.rho[k] = col.rho;
+        O.loops[k] = col.l;
+        O.flags[k] = flags;
+        w.ctr[CTR_QR] += col.c_qr;
+        w.ctr[CTR_RES] += col.c_res;
+        w.ctr[CTR_REFINE] += col.c_ref;
+        w.ctr[CTR_BYTES] += col.c_bytes;
+        w.ctr[CTR_LOOPS] += (double)col.l;
+        w.ctr[CTR_SOLVES] += col.c_solves;
+        w.ctr[CTR_DROPS] += col.c_drops;
+        w.ctr[CTR_PMAX] = fmax(w.ctr[CTR_PMAX], col.c_pmax);
+        w.ctr[CTR_QMAX] = fmax(w.ctr[CTR_QMAX], col.c_qmax);
+        w.ctr[CTR_COLS] += 1.0;
+        w.ctr[CTR_RANK] += col.rank_flag ? 1.0 : 0.0;
+        w.ctr[CTR_NONFINITE] += fin ? 0.0 : 1.0;
+    }
+    team.sync();
+    (void)bin;
+}
+
+template <class Team, typename T>
+__device__ void run_queue(const Team &team, Work<T> &w, const DevA &A, const DevParams &P, const Caps &cap,
+                          const ColQueue &Q, const ColOut &O, double *gctr, bool last_bin, int bin) {
+    const int me = team.rank();
+    for (int i = me; i < CTR_COUNT; i += Team::SIZE) w.ctr[i] = 0.0;
+    team.sync();
+    const int64_t nq = Q.count ? (int64_t)(*(volatile const uint32_t *)Q.count) : Q.n;
+    for (;;) {
+        uint32_t idx = 0;
+        if (me == 0) idx = atomicAdd(Q.next, 1u);
+        idx = team.bcast(idx, 0);
+        if ((int64_t)idx >= nq) break;
+        int32_t k = Q.cols ? Q.cols[idx] : (int32_t)idx;
+        Column<Team, T> col(team, A, P, cap, w, k);
+        int st = col.run();
+        emit_or_forward(team, col, st, Q, O, last_bin, bin);
+    }
+    team.sync();
+    if (me == 0) {
+        for (int i = 0; i < CTR_COUNT; ++i) {
+            if (i == CTR_PMAX || i == CTR_QMAX)
+                atomicMax((unsigned long long *)&gctr[i], (unsigned long long)__double_as_longlong(w.ctr[i]));
+            else if (w.ctr[i] != 0.0)
+                atomicAdd(&gctr[i], w.ctr[i]);
+        }
+        if (w.ctr[CTR_COLS] != 0.0) atomicAdd(&gctr[CTR_COUNT + bin], w.ctr[CTR_COLS]);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_bin_warp(DevA A, DevParams P, Caps cap, ColQueue Q, ColOut O, double *gctr,
+                                                  int last_bin) {
+    extern __shared__ __align__(16) char smem[];
+    const int wid = threadIdx.x >> 5;
+    Work<T> w;
+    w.carve(smem + (size_t)wid * Work<T>::bytes(cap), cap);
+    WarpTeam team;
+    run_queue(team, w, A, P, cap, Q, O, gctr, last_bin != 0, 0);
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_bin_block(DevA A, DevParams P, Caps cap, ColQueue Q, ColOut O, double *gctr,
+                                                  int last_bin, char *gwork, size_t gstride, int bin) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ double redd[NT / 32 + 1];
+    __shared__ int redi[NT / 32 + 1];
+    Work<T> w;
+    if (gwork) w.carve(gwork + (size_t)blockIdx.x * gstride, cap);
+    else w.carve(smem, cap);
+    BlockTeam<NT> team{redd, redi};
+    run_queue(team, w, A, P, cap, Q, O, gctr, last_bin != 0, bin);
+}
+
+// ---------------------------------------------------------------------------
+// statistics over the per-column outputs in a fixed order (deterministic)
+
+__global__ void k_column_stats(const double *rho, const int32_t *flags, const int32_t *len, int64_t n, double eps,
+                               double *out /* [frob2, n_c, nnz] */) {
+    __shared__ double s0[1024], s1[1024], s2[1024];
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+        double r = rho[k];
+        if (!(flags[k] & RSAI_COL_FAILED)) {
+            a += r * r;
+            b += (r > eps) ? 1.0 : 0.0;
+        } else {
+            b += 1.0;
+        }
+        c += (double)len[k];
+    }
+    s0[threadIdx.x] = a; s1[threadIdx.x] = b; s2[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            s0[threadIdx.x] += s0[threadIdx.x + o];
+            s1[threadIdx.x] += s1[threadIdx.x + o];
+            s2[threadIdx.x] += s2[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { out[0] = s0[0]; out[1] = s1[0]; out[2] = s2[0]; }
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of int32 counts into int64 offsets (three passes)
+
+__global__ void k_scan_blocks(const int32_t *in, int64_t n, int64_t *out, int64_t *block_sums) {
+    __shared__ int64_t sh[1024];
+    int64_t i = blockIdx.x * 1024LL + threadIdx.x;
+    int64_t v = (i < n) ? in[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int64_t t = (threadIdx.x >= (unsigned)o) ? sh[threadIdx.x - o] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += t;
+        __syncthreads();
+    }
+    if (i < n) out[i] = sh[threadIdx.x] - v;
+    if (threadIdx.x == 1023) block_sums[blockIdx.x] = sh[1023];
+}
+
+__global__ void k_scan_sums(int64_t *block_sums, int64_t nb, int64_t *total) {
+    // one block: sequential chunks, carried offset
+    __shared__ int64_t sh[1024];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nb; base += 1024) {
+        int64_t i = base + threadIdx.x;
+        int64_t v = (i < nb) ? block_sums[i] : 0;
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            int64_t t = (threadIdx.x >= (unsigned)o) ? sh[threadIdx.x - o] : 0;
+            __syncthreads();
+            sh[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < nb) block_sums[i] = carry + sh[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += sh[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_add(int64_t *out, int64_t n, const int64_t *block_sums, const int64_t *total) {
+    int64_t i = blockIdx.x * 1024LL + threadIdx.x;
+    if (i < n) out[i] += block_sums[blockIdx.x];
+    if (i == 0) out[n] = *total;
+}
+
+// ---------------------------------------------------------------------------
+// assembly of M: pool segments -> CSC -> CSR (rows sorted by column)
+
+// warp per column: copy the column's pool segment to its CSC slot, count rows
+__global__ void k_pool_to_csc(const int64_t *col_off, const int32_t *col_len, const int32_t *pool_rows,
+                              const double *pool_vals, const int64_t *Mcolptr, int32_t *Mrows, double *Mvals,
+                              int32_t *row_count, int64_t n) {
+    int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (k >= n) return;
+    int64_t src = col_off[k], dst = Mcolptr[k];
+    int len = col_len[k];
+    for (int c = lane; c < len; c += 32) {
+        int32_t r = pool_rows[src + c];
+        Mrows[dst + c] = r;
+        Mvals[dst + c] = pool_vals[src + c];
+        atomicAdd(&row_count[r], 1);
+    }
+}
+
+// warp per column: drop each entry into its row (unordered within the row)
+__global__ void k_csc_to_rows(const int64_t *Mcolptr, const int32_t *Mrows, const double *Mvals,
+                              const int64_t *Mrowptr, int32_t *cursor, int32_t *tcols, double *tvals,
+                              int64_t *tsrc, int64_t n) {
+    int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (k >= n) return;
+    for (int64_t e = Mcolptr[k] + lane; e < Mcolptr[k + 1]; e += 32) {
+        int32_t r = Mrows[e];
+        int64_t pos = Mrowptr[r] + atomicAdd(&cursor[r], 1);
+        tcols[pos] = (int32_t)k;
+        tvals[pos] = Mvals[e];
+        tsrc[pos] = e;
+    }
+}
+
+// warp per row: place every entry at its rank among the row's column indices
+__global__ void k_sort_rows(const int64_t *Mrowptr, const int32_t *tcols, const double *tvals, const int64_t *tsrc,
+                            int32_t *Mcols, double *Mvals_csr, int64_t *csc_to_csr_M, int64_t n) {
+    int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    int64_t a = Mrowptr[r], b = Mrowptr[r + 1];
+    for (int64_t e = a + lane; e < b; e += 32) {
+        int32_t key = tcols[e];
+        int64_t rank = 0;
+        for (int64_t f = a; f < b; ++f) rank += (tcols[f] < key);
+        Mcols[a + rank] = key;
+        Mvals_csr[a + rank] = tvals[e];
+        csc_to_csr_M[tsrc[e]] = a + rank;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host-side launchers
+
+template <typename T>
+size_t warp_bin_smem(const Caps &c, int warps) { return (size_t)warps * Work<T>::bytes(c); }
+
+template <typename T>
+size_t work_bytes(const Caps &c) { return Work<T>::bytes(c); }
+
+template size_t work_bytes<float>(const Caps &);
+template size_t work_bytes<double>(const Caps &);
+
+cudaError_t launch_bin_warp(bool fp32, int grid, int warps, const DevA &A, const DevParams &P, const Caps &cap,
+                            const ColQueue &Q, const ColOut &O, double *gctr, bool last, cudaStream_t st) {
+    size_t smem = fp32 ? warp_bin_smem<float>(cap, warps) : warp_bin_smem<double>(cap, warps);
+    if (fp32) {
+        cudaFuncSetAttribute(k_bin_warp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_bin_warp<float><<<grid, warps * 32, smem, st>>>(A, P, cap, Q, O, gctr, last ? 1 : 0);
+    } else {
+        cudaFuncSetAttribute(k_bin_warp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_bin_warp<double><<<grid, warps * 32, smem, st>>>(A, P, cap, Q, O, gctr, last ? 1 : 0);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_block(bool fp32, int grid, const DevA &A, const DevParams &P, const Caps &cap,
+                             const ColQueue &Q, const ColOut &O, double *gctr, bool last, char *gwork,
+                             size_t gstride, int bin, cudaStream_t st) {
+    size_t smem = gwork ? 0 : (fp32 ? Work<float>::bytes(cap) : Work<double>::bytes(cap));
+    if (fp32) {
+        cudaFuncSetAttribute(k_bin_block<float, kBlockThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_bin_block<float, kBlockThreads><<<grid, kBlockThreads, smem, st>>>(A, P, cap, Q, O, gctr, last ? 1 : 0,
+                                                                             gwork, gstride, bin);
+    } else {
+        cudaFuncSetAttribute(k_bin_block<double, kBlockThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_bin_block<double, kBlockThreads><<<grid, kBlockThreads, smem, st>>>(A, P, cap, Q, O, gctr, last ? 1 : 0,
+                                                                              gwork, gstride, bin);
+    }
+    return cudaGetLastError();
+}
+
+int occupancy_bin_warp(bool fp32, int warps, const Caps &cap) {
+    int nb = 0;
+    size_t smem = fp32 ? warp_bin_smem<float>(cap, warps) : warp_bin_smem<double>(cap, warps);
+    if (fp32) {
+        cudaFuncSetAttribute(k_bin_warp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bin_warp<float>, warps * 32, smem);
+    } else {
+        cudaFuncSetAttribute(k_bin_warp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bin_warp<double>, warps * 32, smem);
+    }
+    return nb;
+}
+
+int occupancy_bin_block(bool fp32, const Caps &cap, bool global_work) {
+    int nb = 0;
+    size_t smem = global_work ? 0 : (fp32 ? Work<float>::bytes(cap) : Work<double>::bytes(cap));
+    if (fp32) {
+        cudaFuncSetAttribute(k_bin_block<float, kBlockThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bin_block<float, kBlockThreads>, kBlockThreads, smem);
+    } else {
+        cudaFuncSetAttribute(k_bin_block<double, kBlockThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bin_block<double, kBlockThreads>, kBlockThreads, smem);
+    }
+    return nb;
+}
+
+}  // namespace rsai

@@ -1,0 +1,539 @@
+// column.cuh -- one column of RSAI(tol) on one team (warp or CTA).
+//
+// Per column k (Section 3 Algorithm 1, Section 4 Eq. 4.3):
+//   J = {k}, R = {}, l = 0
+//   solve(J); drop(J); r = A m - e_k on S = I u {k}; rho = ||r||
+//   while rho > eps and l < l_max:
+//     Rhat = top-c of {i in S : |r_i| > band, i not in R} by (|r_i| desc, i asc)
+//            with a tie band; R += Rhat                        (step 4, Eq. 3.2)
+//     Jhat = cols(A(Rhat,:)) \ J                               (step 5)
+//     l += 1; if Jhat is empty: continue                       (step 6)
+//     J += Jhat; solve(J); drop(J); residual                   (step 7, Eq. 4.3)
+//
+// solve(J): I = rows of A(:,J) (Section 2), B = A(I,J) gathered into the team's
+// workspace (column-major, leading dimension q), e = e_k(I), Householder QR of
+// B applied to e, back substitution (Eq. 2.3).  In RSAI_FP32_REFINE the QR runs
+// in float; the residual of the float solution is formed in double from the
+// sparse columns of A, one correction is solved with the float factors and
+// added in double.  The residual r_k, its norm, the dominant-row choice, the
+// drop test and the stopping test are double in both precisions.
+//
+// A column whose problem outgrows the team's workspace returns OVERFLOW; the
+// caller hands it to the next (larger) bin, which restarts it from J = {k}.
+#pragma once
+
+#include "common.cuh"
+
+namespace rsai {
+
+struct Caps {
+    int qcap;      // max |I| (rows of the LS problem); |S| <= qcap + 1
+    int pcap;      // max |J|
+    int scap;      // sort buffer (power of two)
+    int rcap;      // max |R| (dominant rows used so far)
+    int64_t bcap;  // max q*p elements of B
+};
+
+template <typename T> struct Work {
+    T *B, *vhead, *vtv, *rhs;
+    double *m, *r, *ctr;
+    int32_t *I, *S, *J, *Jn, *Rset, *buf, *buf2, *Rhat;
+
+    __host__ __device__ static size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+    __host__ __device__ static size_t bytes(const Caps &c) {
+        size_t b = 0;
+        b += align16(sizeof(T) * (size_t)c.bcap);
+        b += 2 * align16(sizeof(T) * (size_t)c.pcap);
+        b += align16(sizeof(T) * (size_t)(c.qcap + 1));
+        b += align16(sizeof(double) * (size_t)c.pcap);
+        b += align16(sizeof(double) * (size_t)(c.qcap + 1));
+        b += align16(sizeof(double) * CTR_COUNT);
+        b += align16(sizeof(int32_t) * (size_t)c.qcap);
+        b += align16(sizeof(int32_t) * (size_t)(c.qcap + 1));
+        b += 2 * align16(sizeof(int32_t) * (size_t)c.pcap);
+        b += align16(sizeof(int32_t) * (size_t)c.rcap);
+        b += 2 * align16(sizeof(int32_t) * (size_t)c.scap);
+        b += align16(sizeof(int32_t) * 32);
+        return b;
+    }
+    __device__ void carve(char *base, const Caps &c) {
+        size_t o = 0;
+        B = (T *)(base + o); o += align16(sizeof(T) * (size_t)c.bcap);
+        vhead = (T *)(base + o); o += align16(sizeof(T) * (size_t)c.pcap);
+        vtv = (T *)(base + o); o += align16(sizeof(T) * (size_t)c.pcap);
+        rhs = (T *)(base + o); o += align16(sizeof(T) * (size_t)(c.qcap + 1));
+        m = (double *)(base + o); o += align16(sizeof(double) * (size_t)c.pcap);
+        r = (double *)(base + o); o += align16(sizeof(double) * (size_t)(c.qcap + 1));
+        ctr = (double *)(base + o); o += align16(sizeof(double) * CTR_COUNT);
+        I = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.qcap);
+        S = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)(c.qcap + 1));
+        J = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.pcap);
+        Jn = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.pcap);
+        Rset = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.rcap);
+        buf = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.scap);
+        buf2 = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.scap);
+        Rhat = (int32_t *)(base + o); o += align16(sizeof(int32_t) * 32);
+    }
+};
+
+enum ColStatus { COL_DONE = 0, COL_OVERFLOW = 1 };
+
+__host__ __device__ inline int next_pow2(int x) {
+    int n = 1;
+    while (n < x) n <<= 1;
+    return n;
+}
+
+// Algorithmic flops of one solve on (q,p) appended to a factorisation of
+// (q0,p0) (p0 = 0: from scratch): the reflectors of the old columns applied to
+// the new ones, Householder steps p0..p-1 on the stacked rows (norm, then every
+// trailing column and the right-hand side), and the back substitution.
+__device__ __forceinline__ double solve_flops(int64_t q0, int64_t p0, int64_t q, int64_t p) {
+    int64_t mm = p - p0;
+    int64_t f = 4 * mm * (p0 * q0 - p0 * (p0 - 1) / 2);
+    int64_t s2 = mm * (mm + 1) * (2 * mm + 1) / 6;
+    f += (q - p) * (2 * mm + 2 * mm * (mm + 1)) + mm * (mm + 1) + 4 * s2;
+    return (double)(f + p * p);
+}
+
+template <class Team, typename T> struct Column {
+    const Team &team;
+    const DevA &A;
+    const DevParams &P;
+    const Caps &cap;
+    Work<T> &w;
+    int32_t k;
+    int p, q, s, nR, l;
+    int64_t q0, p0;
+    int rank_flag;
+    double rho;
+    // per-column work counters (committed only when the column finishes)
+    double c_qr, c_res, c_ref, c_bytes, c_solves, c_drops, c_pmax, c_qmax;
+
+    __device__ Column(const Team &t, const DevA &a, const DevParams &pp, const Caps &c, Work<T> &ww, int32_t kk)
+        : team(t), A(a), P(pp), cap(c), w(ww), k(kk) {}
+
+    // I = sorted rows of A(:,J) (Section 2).  Returns false on overflow.
+    __device__ bool rows_of_J() {
+        int base = 0;
+        for (int c0 = 0; c0 < p; c0 += Team::SIZE) {
+            int c = c0 + team.rank();
+            int len = 0;
+            int64_t st = 0;
+            if (c < p) {
+                st = A.col_ptr[w.J[c]];
+                len = (int)(A.col_ptr[w.J[c] + 1] - st);
+            }
+            int tot;
+            int off = team.scan(len, &tot);
+            if (next_pow2(base + tot) > cap.scap) return false;
+            for (int e = 0; e < len; ++e) w.buf[base + off + e] = A.row_idx[st + e];
+            base += tot;
+        }
+        team.sync();
+        team_sort_i32(team, w.buf, base);
+        int nq = team_unique_i32(team, w.buf, base, w.buf2);
+        if (nq > cap.qcap) return false;
+        for (int i = team.rank(); i < nq; i += Team::SIZE) w.I[i] = w.buf2[i];
+        q = nq;
+        team.sync();
+        return true;
+    }
+
+    // Householder QR of B (q x p, ld q) applied to rhs, then back substitution
+    // into rhs[0..p).  Keeps the reflectors (v_j below the diagonal of B,
+    // heads in vhead, v^T v in vtv) for the refinement solve.
+    __device__ void qr_solve(T small) {
+        const int me = team.rank();
+        for (int j = 0; j < p; ++j) {
+            T *col = w.B + (int64_t)j * q;
+            T part = 0;
+            for (int i = me; i < q; i += Team::SIZE)
+                if (i >= j) part += col[i] * col[i];
+            T sigma = team.sum(part);
+            T x0 = col[j];
+            T nrm = sqrt(sigma);
+            T alpha = (x0 >= T(0)) ? -nrm : nrm;
+            T v0 = x0 - alpha;
+            T vtv = sigma - x0 * x0 + v0 * v0;
+            if (vtv > T(0)) {
+                for (int c = j + 1; c <= p; ++c) {
+                    T *t = (c < p) ? w.B + (int64_t)c * q : w.rhs;
+                    T d = 0;
+                    for (int i = me; i < q; i += Team::SIZE)
+                        if (i >= j) d += ((i == j) ? v0 : col[i]) * t[i];
+                    T sdot = team.sum(d);
+                    T f = T(2) * sdot / vtv;
+                    for (int i = me; i < q; i += Team::SIZE)
+                        if (i >= j) t[i] -= f * ((i == j) ? v0 : col[i]);
+                }
+            }
+            team.sync();
+            if (me == 0) {
+                col[j] = alpha;
+                w.vhead[j] = v0;
+                w.vtv[j] = vtv;
+                if (fabs((double)alpha) <= (double)small) rank_flag = 1;
+            }
+            team.sync();
+        }
+        rank_flag = team.maxi(rank_flag);
+        back_substitute(small);
+    }
+
+    // rhs[0..p) <- R^{-1} rhs[0..p) (column-oriented, in place)
+    __device__ void back_substitute(T small) {
+        const int me = team.rank();
+        for (int i = p - 1; i >= 0; --i) {
+            T d = w.B[(int64_t)i * q + i];
+            T xi = (fabs((double)d) <= (double)small) ? T(0) : w.rhs[i] / d;
+            team.sync();
+            for (int c = me; c < i; c += Team::SIZE) w.rhs[c] -= w.B[(int64_t)i * q + c] * xi;
+            if (me == 0) w.rhs[i] = xi;
+            team.sync();
+        }
+    }
+
+    // rhs <- Q^T rhs with the stored reflectors, then R^{-1}
+    __device__ void apply_qt_solve(T small) {
+        const int me = team.rank();
+        for (int j = 0; j < p; ++j) {
+            const T *col = w.B + (int64_t)j * q;
+            T v0 = w.vhead[j], vtv = w.vtv[j];
+            if (vtv > T(0)) {
+                T d = 0;
+                for (int i = me; i < q; i += Team::SIZE)
+                    if (i >= j) d += ((i == j) ? v0 : col[i]) * w.rhs[i];
+                T sdot = team.sum(d);
+                T f = T(2) * sdot / vtv;
+                for (int i = me; i < q; i += Team::SIZE)
+                    if (i >= j) w.rhs[i] -= f * ((i == j) ? v0 : col[i]);
+            }
+            team.sync();
+        }
+        back_substitute(small);
+    }
+
+    // S = I u {k}; r = A(:,J) m - e_k on S in double (Eq. 2.4), row by row
+    // through the CSR of A (ascending j, so the sum order is fixed).
+    // `refine`: the residual of a refinement step (counted as refinement work).
+    __device__ void residual(bool refine = false) {
+        const int me = team.rank();
+        int pk = lower_bound_i32(w.I, q, k);
+        bool has_k = pk < q && w.I[pk] == k;
+        s = has_k ? q : q + 1;
+        for (int i = me; i < s; i += Team::SIZE) {
+            int32_t row;
+            if (has_k) row = w.I[i];
+            else row = (i < pk) ? w.I[i] : (i == pk ? k : w.I[i - 1]);
+            w.S[i] = row;
+        }
+        team.sync();
+        double ss = 0.0, cnt = 0.0;
+        for (int i = me; i < s; i += Team::SIZE) {
+            int32_t row = w.S[i];
+            double acc = 0.0;
+            for (int64_t e = A.row_ptr[row]; e < A.row_ptr[row + 1]; ++e) {
+                int pos = find_i32(w.J, p, A.col_idx[e]);
+                if (pos >= 0) { acc = fma(A.val[e], w.m[pos], acc); cnt += 1.0; }
+            }
+            if (row == k) acc -= 1.0;
+            w.r[i] = acc;
+            ss += acc * acc;
+        }
+        rho = sqrt(team.sum(ss));
+        double nnzJ = team.sum(cnt);
+        if (refine) c_ref += 2.0 * nnzJ + 2.0 * (double)s;
+        else c_res += 2.0 * nnzJ + 2.0 * (double)s;
+        team.sync();
+    }
+
+    // Solve the LS problem on the current J (Eq. 2.3).  `append`: J extends the
+    // previously solved J (the paper's QR update; counted as such).
+    __device__ bool solve(bool append) {
+        const int me = team.rank();
+        if (!rows_of_J()) return false;
+        if ((int64_t)q * p > cap.bcap) return false;
+        // B = A(I,J), zero-filled
+        int64_t qp = (int64_t)q * p;
+        for (int64_t i = me; i < qp; i += Team::SIZE) w.B[i] = T(0);
+        for (int i = me; i < q; i += Team::SIZE) w.rhs[i] = (w.I[i] == k) ? T(1) : T(0);
+        team.sync();
+        double fro2 = 0.0;
+        for (int c = me; c < p; c += Team::SIZE) {
+            int32_t j = w.J[c];
+            for (int64_t e = A.col_ptr[j]; e < A.col_ptr[j + 1]; ++e) {
+                int pos = find_i32(w.I, q, A.row_idx[e]);
+                double a = A.cval[e];
+                w.B[(int64_t)c * q + pos] = (T)a;
+                fro2 += a * a;
+            }
+        }
+        double fro = sqrt(team.sum(fro2));
+        team.sync();
+        T small = (T)((double)q * Unit<T>::u * 2.0 * fro);
+        rank_flag = 0;
+        if (q < p) {  // more unknowns than rows: only possible for singular A
+            for (int c = me; c < p; c += Team::SIZE) w.m[c] = 0.0;
+            rank_flag = 1;
+            team.sync();
+        } else {
+            qr_solve(small);
+            for (int c = me; c < p; c += Team::SIZE) w.m[c] = (double)w.rhs[c];
+            team.sync();
+            if (P.precision == RSAI_FP32_REFINE) {
+                // one step of refinement: r = B m - e in double, m += R^{-1} Q^T (-r)
+                residual(true);
+                int pk = lower_bound_i32(w.I, q, k);
+                bool has_k = pk < q && w.I[pk] == k;
+                for (int i = me; i < q; i += Team::SIZE) {
+                    int si = (has_k || i < pk) ? i : i + 1;
+                    w.rhs[i] = (T)(-w.r[si]);
+                }
+                team.sync();
+                apply_qt_solve(small);
+                for (int c = me; c < p; c += Team::SIZE) w.m[c] += (double)w.rhs[c];
+                team.sync();
+                c_ref += 4.0 * (double)q * (double)p + (double)p * (double)p;
+            }
+        }
+        c_qr += append ? solve_flops(q0, p0, q, p) : solve_flops(0, 0, q, p);
+        q0 = q;
+        p0 = p;
+        c_solves += 1.0;
+        c_pmax = fmax(c_pmax, (double)p);
+        c_qmax = fmax(c_qmax, (double)q);
+        return true;
+    }
+
+    // Eq. 4.3: drop |m_j| <= tau, keep at least the largest, re-solve once.
+    __device__ bool drop() {
+        if (P.drop_mode == RSAI_DROP_NONE) return true;
+        const int me = team.rank();
+        const double nrm1 = *P.norm1;
+        double tau = (P.drop_mode == RSAI_DROP_ADAPTIVE) ? P.eps / ((double)p * nrm1) : P.tol / nrm1;
+        int nkeep = 0;
+        double ba = -1.0;
+        int bi = INT32_MAX;
+        for (int c = me; c < p; c += Team::SIZE) {
+            double a = fabs(w.m[c]);
+            nkeep += (a > tau);
+            if (dom_before(a, c, ba, bi)) { ba = a; bi = c; }
+        }
+        int keep_total;
+        {
+            int tot = 0;
+            int part = nkeep;
+            tot = (int)team.sum((double)part);
+            keep_total = tot;
+        }
+        if (keep_total == p) return true;
+        if (keep_total == 0) {
+            team.argmax(ba, bi);
+            if (p == 1) return true;
+            int32_t jb = w.J[bi];
+            team.sync();
+            if (me == 0) w.J[0] = jb;
+            p = 1;
+            team.sync();
+        } else {
+            int base = 0;
+            for (int c0 = 0; c0 < p; c0 += Team::SIZE) {
+                int c = c0 + me;
+                int f = (c < p) && (fabs(w.m[c]) > tau);
+                int tot;
+                int pos = team.scan(f, &tot);
+                if (f) w.Jn[base + pos] = w.J[c];
+                base += tot;
+            }
+            team.sync();
+            for (int c = me; c < base; c += Team::SIZE) w.J[c] = w.Jn[c];
+            p = base;
+            team.sync();
+        }
+        c_drops += 1.0;
+        return solve(false);
+    }
+
+    // Top-c dominant rows of S \ R (Algorithm 1 step 4) into w.Rhat; returns
+    // their number (0: no candidate left).
+    __device__ int dominant_rows() {
+        const int me = team.rank();
+        double rinf = 0.0;
+        for (int i = me; i < s; i += Team::SIZE) rinf = fmax(rinf, fabs(w.r[i]));
+        rinf = team.maxv(rinf);
+        const double band = P.tie_band * rinf;
+        int ncand = 0;
+        for (int i = me; i < s; i += Team::SIZE) {
+            double a = fabs(w.r[i]);
+            ncand += (a > band) && (find_i32(w.Rset, nR, w.S[i]) < 0);
+        }
+        ncand = (int)team.sum((double)ncand);
+        if (ncand == 0) return 0;
+        const int c = P.c;
+        bool take_all = ncand <= c;
+        double v = 0.0;
+        if (!take_all) {
+            // the c-th element of the (|r| desc, i asc) order: c rounds of argmax,
+            // each over the candidates strictly after the previous pick
+            double pa = INFINITY;
+            int pi = -1;
+            for (int t = 0; t < c; ++t) {
+                double ba = -1.0;
+                int bi = INT32_MAX;
+                for (int i = me; i < s; i += Team::SIZE) {
+                    double a = fabs(w.r[i]);
+                    int32_t row = w.S[i];
+                    if (a > band && dom_before(pa, pi, a, row) && dom_before(a, row, ba, bi) &&
+                        find_i32(w.Rset, nR, row) < 0) {
+                        ba = a;
+                        bi = row;
+                    }
+                }
+                team.argmax(ba, bi);
+                pa = ba;
+                pi = bi;
+            }
+            v = pa;
+        }
+        // selection in index order: all candidates, or (above the band) +
+        // (lowest-index ties up to c)
+        int nabove = 0;
+        if (!take_all) {
+            for (int i = me; i < s; i += Team::SIZE) {
+                double a = fabs(w.r[i]);
+                nabove += (a > band) && (a - v > band) && (find_i32(w.Rset, nR, w.S[i]) < 0);
+            }
+            nabove = (int)team.sum((double)nabove);
+        }
+        const int need = c - nabove;
+        int base = 0, tbase = 0;
+        for (int i0 = 0; i0 < s; i0 += Team::SIZE) {
+            int i = i0 + me;
+            int cand = 0, above = 0, tie = 0;
+            if (i < s) {
+                double a = fabs(w.r[i]);
+                cand = (a > band) && (find_i32(w.Rset, nR, w.S[i]) < 0);
+                if (cand && !take_all) {
+                    above = (a - v > band);
+                    tie = (fabs(a - v) <= band);
+                }
+            }
+            int ttot;
+            int trank = team.scan(tie, &ttot);
+            int sel = take_all ? cand : (above || (tie && (tbase + trank) < need));
+            int tot;
+            int pos = team.scan(sel, &tot);
+            if (sel) w.Rhat[base + pos] = w.S[i];
+            base += tot;
+            tbase += ttot;
+        }
+        team.sync();
+        return base;
+    }
+
+    // R = R u Rhat (sorted); false if R outgrows its capacity
+    __device__ bool add_to_R(int nh) {
+        if (nR + nh > cap.rcap) return false;
+        if (team.rank() == 0) {
+            for (int t = 0; t < nh; ++t) {
+                int32_t x = w.Rhat[t];
+                int at = nR + t;
+                while (at > 0 && w.Rset[at - 1] > x) { w.Rset[at] = w.Rset[at - 1]; --at; }
+                w.Rset[at] = x;
+            }
+        }
+        nR += nh;
+        team.sync();
+        return true;
+    }
+
+    // Jhat = cols(A(Rhat,:)) \ J into w.buf; returns |Jhat| or -1 on overflow
+    __device__ int new_columns(int nh) {
+        const int me = team.rank();
+        int len = 0;
+        int64_t st = 0;
+        if (me < nh) {
+            st = A.row_ptr[w.Rhat[me]];
+            len = (int)(A.row_ptr[w.Rhat[me] + 1] - st);
+        }
+        int tot;
+        int off = team.scan(len, &tot);
+        if (next_pow2(tot) > cap.scap) return -1;
+        for (int e = 0; e < len; ++e) w.buf[off + e] = A.col_idx[st + e];
+        team.sync();
+        team_sort_i32(team, w.buf, tot);
+        int nu = team_unique_i32(team, w.buf, tot, w.buf2);
+        int base = 0;
+        for (int i0 = 0; i0 < nu; i0 += Team::SIZE) {
+            int i = i0 + me;
+            int f = (i < nu) && (find_i32(w.J, p, w.buf2[i]) < 0);
+            int t2;
+            int pos = team.scan(f, &t2);
+            if (f) w.buf[base + pos] = w.buf2[i];
+            base += t2;
+        }
+        team.sync();
+        return base;
+    }
+
+    // J = J u Jhat (both sorted, disjoint) by merge ranks
+    __device__ bool merge_J(int nj) {
+        const int me = team.rank();
+        if (p + nj > cap.pcap) return false;
+        for (int a = me; a < p; a += Team::SIZE) w.Jn[a + lower_bound_i32(w.buf, nj, w.J[a])] = w.J[a];
+        for (int b = me; b < nj; b += Team::SIZE) w.Jn[b + lower_bound_i32(w.J, p, w.buf[b])] = w.buf[b];
+        team.sync();
+        p += nj;
+        for (int a = me; a < p; a += Team::SIZE) w.J[a] = w.Jn[a];
+        team.sync();
+        return true;
+    }
+
+    // algorithmic bytes of columns entering J: 12 per nonzero + 16 of pointers
+    __device__ void note_bytes_columns(int from, int count, const int32_t *list) {
+        double b = 0.0;
+        for (int t = from + team.rank(); t < from + count; t += Team::SIZE) {
+            int32_t j = list[t];
+            b += 12.0 * (double)(A.col_ptr[j + 1] - A.col_ptr[j]) + 16.0;
+        }
+        c_bytes += team.sum(b);
+    }
+
+    // Runs the whole column.  Returns COL_DONE or COL_OVERFLOW.
+    __device__ int run() {
+        const int me = team.rank();
+        p = 1; q = 0; s = 0; nR = 0; l = 0; q0 = 0; p0 = 0; rank_flag = 0; rho = 0.0;
+        c_qr = c_res = c_ref = c_bytes = c_solves = c_drops = 0.0;
+        c_pmax = c_qmax = 0.0;
+        if (me == 0) w.J[0] = k;
+        team.sync();
+        c_bytes += 12.0 * (double)(A.col_ptr[k + 1] - A.col_ptr[k]) + 16.0;
+        if (!solve(false)) return COL_OVERFLOW;
+        if (!drop()) return COL_OVERFLOW;
+        residual();
+        while (rho > P.eps && l < P.l_max) {
+            int nh = dominant_rows();
+            if (nh == 0) break;
+            if (!add_to_R(nh)) return COL_OVERFLOW;
+            {
+                double b = 0.0;
+                if (me < nh) b = 4.0 * (double)(A.row_ptr[w.Rhat[me] + 1] - A.row_ptr[w.Rhat[me]]) + 16.0;
+                c_bytes += team.sum(b);
+            }
+            int nj = new_columns(nh);
+            if (nj < 0) return COL_OVERFLOW;
+            ++l;
+            if (nj == 0) continue;
+            note_bytes_columns(0, nj, w.buf);
+            if (!merge_J(nj)) return COL_OVERFLOW;
+            if (!solve(true)) return COL_OVERFLOW;
+            if (!drop()) return COL_OVERFLOW;
+            residual();
+        }
+        c_bytes += 36.0 * (double)p;
+        return COL_DONE;
+    }
+};
+
+}  // namespace rsai

@@ -1,0 +1,267 @@
+// common.cuh -- device-side building blocks shared by the RSAI kernels.
+//
+// A "team" is the group of threads that works on one column of M at a time:
+// a warp (WarpTeam) for small least-squares problems, a whole CTA (BlockTeam)
+// for larger ones.  The column algorithm (column.cuh) is written once against
+// this interface: rank()/size, sync(), sums, maxima, argmax with a
+// (value desc, index asc) order, exclusive scans and a bitonic sort.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rsai.h"
+
+namespace rsai {
+
+// ----------------------------------------------------------------------------
+// Device view of A (CSR for rows A(i,:), CSC for columns A(:,j); Section 2).
+struct DevA {
+    int64_t n;
+    const int64_t *row_ptr;
+    const int32_t *col_idx;
+    const double *val;
+    const int64_t *col_ptr;
+    const int32_t *row_idx;
+    const double *cval;
+};
+
+// Parameters as the kernels see them (rsai_params plus derived values).
+struct DevParams {
+    int c, l_max, drop_mode, precision;
+    double eps, tol, tie_band;
+    const double *norm1;  // ||A||_1 on the device (computed by a kernel)
+};
+
+// Work counters of one team, summed into the global statistics at the end.
+enum Counter {
+    CTR_QR = 0, CTR_RES, CTR_REFINE, CTR_BYTES, CTR_LOOPS, CTR_SOLVES, CTR_DROPS,
+    CTR_PMAX, CTR_QMAX, CTR_COLS, CTR_RANK, CTR_NONFINITE, CTR_NC, CTR_FROB2, CTR_FAILED,
+    CTR_COUNT
+};
+
+// Per-column outputs.
+struct ColOut {
+    int64_t *col_off;   // offset of the column in the result pool
+    int32_t *col_len;   // nnz(m_k)
+    double *rho;        // ||r_k||
+    int32_t *loops;
+    int32_t *flags;     // RSAI_COL_*
+    int32_t *pool_rows; // J_k (ascending)
+    double *pool_vals;  // m_k(J_k)
+    int64_t pool_cap;
+    unsigned long long *pool_top;
+    int32_t *err;       // first device error code (0 = none)
+};
+
+// Queue of columns for one bin.
+struct ColQueue {
+    const int32_t *cols;      // explicit list (NULL = 0..n-1)
+    const uint32_t *count;    // length of the list on the device (NULL = use n)
+    int64_t n;
+    uint32_t *next;           // work counter (zeroed before the launch)
+    int32_t *ovf_cols;        // where columns that outgrow the bin go
+    uint32_t *ovf_count;
+    int64_t ovf_cap;
+};
+
+// ----------------------------------------------------------------------------
+template <typename T> struct Unit;
+template <> struct Unit<float> { static constexpr double u = 5.9604644775390625e-08; };
+template <> struct Unit<double> { static constexpr double u = 1.1102230246251565e-16; };
+
+__device__ __forceinline__ int lower_bound_i32(const int32_t *a, int len, int32_t v) {
+    int lo = 0, hi = len;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int find_i32(const int32_t *a, int len, int32_t v) {
+    int p = lower_bound_i32(a, len, v);
+    return (p < len && a[p] == v) ? p : -1;
+}
+
+// (a, i) ordered by a descending, then i ascending: true if (a,i) comes first.
+__device__ __forceinline__ bool dom_before(double a, int i, double b, int j) {
+    return a > b || (a == b && i < j);
+}
+
+// ----------------------------------------------------------------------------
+struct WarpTeam {
+    static constexpr int SIZE = 32;
+    __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+    template <typename V> __device__ __forceinline__ V sum(V x) const {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        return x;
+    }
+    __device__ __forceinline__ double maxv(double x) const {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+        return x;
+    }
+    __device__ __forceinline__ int maxi(int x) const {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
+        return x;
+    }
+    // argmax under dom_before; returns the winner to every lane
+    __device__ __forceinline__ void argmax(double &a, int &i) const {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double b = __shfl_xor_sync(0xffffffffu, a, o);
+            int j = __shfl_xor_sync(0xffffffffu, i, o);
+            if (dom_before(b, j, a, i)) { a = b; i = j; }
+        }
+    }
+    // exclusive prefix sum over ranks; *total gets the sum
+    __device__ __forceinline__ int scan(int x, int *total) const {
+        int lane = rank();
+        int inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        *total = __shfl_sync(0xffffffffu, inc, 31);
+        return inc - x;
+    }
+    template <typename V> __device__ __forceinline__ V bcast(V x, int src) const {
+        return __shfl_sync(0xffffffffu, x, src);
+    }
+};
+
+// A whole CTA of NT threads; `red` is NT/32+1 doubles and ints of shared scratch.
+template <int NT> struct BlockTeam {
+    static constexpr int SIZE = NT;
+    static constexpr int NW = NT / 32;
+    double *redd;
+    int *redi;
+    __device__ __forceinline__ int rank() const { return threadIdx.x; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    template <typename V> __device__ __forceinline__ V sum(V x) const {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) redd[threadIdx.x >> 5] = (double)x;
+        __syncthreads();
+        V s = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) s += (V)redd[w];
+        return s;
+    }
+    __device__ __forceinline__ double maxv(double x) const {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) redd[threadIdx.x >> 5] = x;
+        __syncthreads();
+        double s = redd[0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) s = fmax(s, redd[w]);
+        return s;
+    }
+    __device__ __forceinline__ int maxi(int x) const {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) redi[threadIdx.x >> 5] = x;
+        __syncthreads();
+        int s = redi[0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) s = max(s, redi[w]);
+        return s;
+    }
+    __device__ __forceinline__ void argmax(double &a, int &i) const {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double b = __shfl_xor_sync(0xffffffffu, a, o);
+            int j = __shfl_xor_sync(0xffffffffu, i, o);
+            if (dom_before(b, j, a, i)) { a = b; i = j; }
+        }
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) { redd[threadIdx.x >> 5] = a; redi[threadIdx.x >> 5] = i; }
+        __syncthreads();
+        a = redd[0];
+        i = redi[0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w)
+            if (dom_before(redd[w], redi[w], a, i)) { a = redd[w]; i = redi[w]; }
+    }
+    __device__ __forceinline__ int scan(int x, int *total) const {
+        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        int inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        __syncthreads();
+        if (lane == 31) redi[w] = inc;
+        __syncthreads();
+        int before = 0, tot = 0;
+#pragma unroll
+        for (int v = 0; v < NW; ++v) {
+            int s = redi[v];
+            if (v < w) before += s;
+            tot += s;
+        }
+        *total = tot;
+        return before + inc - x;
+    }
+    template <typename V> __device__ __forceinline__ V bcast(V x, int src) const {
+        __syncthreads();
+        if ((int)threadIdx.x == src) redd[NW] = (double)x;
+        __syncthreads();
+        return (V)redd[NW];
+    }
+};
+
+// Bitonic sort of buf[0..len) ascending; buf must have room for the next
+// power of two (padded with INT32_MAX).
+template <class Team>
+__device__ void team_sort_i32(const Team &team, int32_t *buf, int len) {
+    int N = 1;
+    while (N < len) N <<= 1;
+    for (int i = len + team.rank(); i < N; i += Team::SIZE) buf[i] = INT32_MAX;
+    team.sync();
+    for (int k = 2; k <= N; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = team.rank(); i < N; i += Team::SIZE) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    int32_t a = buf[i], b = buf[ixj];
+                    bool up = (i & k) == 0;
+                    if ((a > b) == up) { buf[i] = b; buf[ixj] = a; }
+                }
+            }
+            team.sync();
+        }
+    }
+}
+
+// out = unique(sorted in[0..len)); returns the count (identical on all ranks).
+template <class Team>
+__device__ int team_unique_i32(const Team &team, const int32_t *in, int len, int32_t *out) {
+    int base = 0;
+    for (int c0 = 0; c0 < len; c0 += Team::SIZE) {
+        int i = c0 + team.rank();
+        int f = (i < len) && (i == 0 || in[i] != in[i - 1]);
+        int tot;
+        int pos = team.scan(f, &tot);
+        if (f) out[base + pos] = in[i];
+        base += tot;
+    }
+    team.sync();
+    return base;
+}
+
+__device__ __forceinline__ void set_error(int32_t *err, int code) {
+    atomicCAS(err, 0, code);
+}
+
+}  // namespace rsai

@@ -1,0 +1,52 @@
+// kernels.h -- declarations shared by the host code and the kernel files.
+#pragma once
+
+#include "column.cuh"
+
+namespace rsai {
+
+constexpr int kBlockThreads = 256;  // CTA team size of bins C and G
+constexpr int kWarpsPerCta = 4;     // warps per CTA in bin W
+
+// input checks, ||A||_1, statistics, scan, assembly
+__global__ void k_check_ptr(const int64_t *ptr, int64_t n, int64_t nnz, int32_t *err);
+__global__ void k_check_idx(const int64_t *ptr, const int32_t *idx, int64_t n, int32_t *err, int empty_is_error);
+__global__ void k_csc_map(DevA A, int64_t *csc_to_csr, int32_t *err);
+__global__ void k_csc_from_csr(const double *csr_val, const int64_t *csc_to_csr, double *cval, int64_t nnz);
+__global__ void k_norm1(const int64_t *col_ptr, const double *cval, int64_t n, double *out);
+__global__ void k_column_stats(const double *rho, const int32_t *flags, const int32_t *len, int64_t n, double eps,
+                               double *out);
+__global__ void k_scan_blocks(const int32_t *in, int64_t n, int64_t *out, int64_t *block_sums);
+__global__ void k_scan_sums(int64_t *block_sums, int64_t nb, int64_t *total);
+__global__ void k_scan_add(int64_t *out, int64_t n, const int64_t *block_sums, const int64_t *total);
+__global__ void k_pool_to_csc(const int64_t *col_off, const int32_t *col_len, const int32_t *pool_rows,
+                              const double *pool_vals, const int64_t *Mcolptr, int32_t *Mrows, double *Mvals,
+                              int32_t *row_count, int64_t n);
+__global__ void k_csc_to_rows(const int64_t *Mcolptr, const int32_t *Mrows, const double *Mvals,
+                              const int64_t *Mrowptr, int32_t *cursor, int32_t *tcols, double *tvals,
+                              int64_t *tsrc, int64_t n);
+__global__ void k_sort_rows(const int64_t *Mrowptr, const int32_t *tcols, const double *tvals, const int64_t *tsrc,
+                            int32_t *Mcols, double *Mvals_csr, int64_t *csc_to_csr_M, int64_t n);
+
+template <typename T> size_t work_bytes(const Caps &c);
+
+cudaError_t launch_bin_warp(bool fp32, int grid, int warps, const DevA &A, const DevParams &P, const Caps &cap,
+                            const ColQueue &Q, const ColOut &O, double *gctr, bool last, cudaStream_t st);
+cudaError_t launch_bin_block(bool fp32, int grid, const DevA &A, const DevParams &P, const Caps &cap,
+                             const ColQueue &Q, const ColOut &O, double *gctr, bool last, char *gwork,
+                             size_t gstride, int bin, cudaStream_t st);
+int occupancy_bin_warp(bool fp32, int warps, const Caps &cap);
+int occupancy_bin_block(bool fp32, const Caps &cap, bool global_work);
+
+// apply / solver kernels (apply_kernels.cu)
+cudaError_t launch_spmv(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const double *val,
+                        const double *x, double *y, cudaStream_t st);
+cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *partials, double *out, cudaStream_t st);
+int bicgstab_run(int64_t n, const int64_t *Arp, const int32_t *Aci, const double *Av, const int64_t *Mrp,
+                 const int32_t *Mci, const double *Mv, const double *b, double *x, double rtol, int maxit,
+                 int *iters, double *relres, cudaStream_t st);
+
+// FMA-chain peak (peak_kernels.cu)
+cudaError_t run_peak_fma(bool fp64, cudaStream_t st, double *flops_per_s);
+
+}  // namespace rsai

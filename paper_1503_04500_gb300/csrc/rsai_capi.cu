@@ -1,0 +1,514 @@
+// rsai_capi.cu -- host side of the C ABI declared in include/rsai.h.
+//
+// A handle owns: a device copy of A (CSR + CSC + the CSC->CSR position map),
+// the per-column outputs, the result pool, the overflow queues of the size
+// bins, M in CSC and CSR, and the CUDA graph of the build sequence.  All device
+// memory is taken with cudaMallocAsync on the caller's stream and released
+// with cudaFreeAsync; nothing is allocated by the build sequence itself, so
+// rsai_rebuild can replay it as one CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.h"
+
+using namespace rsai;
+
+struct rsai_handle {
+    int device = 0;
+    int sms = 0;
+    int64_t n = 0, nnz = 0;
+    rsai_params params{};
+    // A on the device
+    int64_t *row_ptr = nullptr, *col_ptr = nullptr, *csc_to_csr = nullptr;
+    int32_t *col_idx = nullptr, *row_idx = nullptr;
+    double *val = nullptr, *cval = nullptr;
+    // scalars / counters: [0] norm1, [1..] gctr (CTR_COUNT + 3), then column stats (3)
+    double *dscal = nullptr;
+    int32_t *err = nullptr;
+    uint32_t *qnext = nullptr;   // [3] queue counters, [3..4] overflow counts
+    int32_t *ovf1 = nullptr, *ovf2 = nullptr;
+    int64_t ovf_cap = 0;
+    // per column
+    int64_t *col_off = nullptr;
+    int32_t *col_len = nullptr, *loops = nullptr, *flags = nullptr;
+    double *rho = nullptr;
+    // pool
+    int32_t *pool_rows = nullptr;
+    double *pool_vals = nullptr;
+    int64_t pool_cap = 0;
+    unsigned long long *pool_top = nullptr;
+    // M
+    int64_t *Mcolptr = nullptr, *Mrowptr = nullptr, *Mcsc_to_csr = nullptr, *tsrc = nullptr;
+    int32_t *Mrows = nullptr, *Mcols = nullptr, *row_count = nullptr, *cursor = nullptr, *tcols = nullptr;
+    double *Mvals_csc = nullptr, *Mvals = nullptr, *tvals = nullptr;
+    int64_t *scan_tmp = nullptr;
+    int64_t scan_tmp_len = 0;
+    // bin G slab
+    char *gwork = nullptr;
+    size_t gstride = 0;
+    int grid_g = 0;
+    // bins
+    Caps capW{}, capC{}, capG{};
+    int grid_w = 0, grid_c = 0;
+    // graph
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    // host copy of the last statistics
+    std::vector<void *> allocs;
+    cudaStream_t alloc_stream = nullptr;
+};
+
+namespace {
+
+constexpr int kScalars = 1 + CTR_COUNT + 3 + 3;
+constexpr int kStatsAt = 1 + CTR_COUNT + 3;
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? RSAI_OK : RSAI_ERR_CUDA; }
+
+template <typename P> int dalloc(rsai_handle *h, P **ptr, size_t count, cudaStream_t st) {
+    void *p = nullptr;
+    size_t bytes = sizeof(P) * (count ? count : 1);
+    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        return RSAI_ERR_OOM;
+    }
+    h->allocs.push_back(p);
+    *ptr = (P *)p;
+    return RSAI_OK;
+}
+
+// copy host or device memory into a device buffer
+cudaError_t to_device(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st);
+}
+
+DevA dev_a(const rsai_handle *h) {
+    return DevA{h->n, h->row_ptr, h->col_idx, h->val, h->col_ptr, h->row_idx, h->cval};
+}
+
+DevParams dev_params(const rsai_handle *h) {
+    DevParams P;
+    P.c = h->params.c;
+    P.l_max = h->params.l_max;
+    P.drop_mode = h->params.drop_mode;
+    P.precision = h->params.precision;
+    P.eps = h->params.eps;
+    P.tol = h->params.tol;
+    P.tie_band = h->params.tie_band;
+    P.norm1 = h->dscal;
+    return P;
+}
+
+unsigned blocks(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+cudaError_t scan_counts(rsai_handle *h, const int32_t *in, int64_t *out, cudaStream_t st) {
+    int64_t nb = (h->n + 1023) / 1024;
+    if (nb < 1) nb = 1;
+    k_scan_blocks<<<(unsigned)nb, 1024, 0, st>>>(in, h->n, out, h->scan_tmp);
+    k_scan_sums<<<1, 1024, 0, st>>>(h->scan_tmp, nb, h->scan_tmp + h->scan_tmp_len - 1);
+    k_scan_add<<<(unsigned)nb, 1024, 0, st>>>(out, h->n, h->scan_tmp, h->scan_tmp + h->scan_tmp_len - 1);
+    return cudaGetLastError();
+}
+
+// The build sequence: no allocation, no host synchronisation (capturable).
+cudaError_t enqueue_build(rsai_handle *h, cudaStream_t st) {
+    const int64_t n = h->n;
+    cudaMemsetAsync(h->dscal, 0, sizeof(double) * kScalars, st);
+    cudaMemsetAsync(h->err, 0, sizeof(int32_t), st);
+    cudaMemsetAsync(h->qnext, 0, sizeof(uint32_t) * 8, st);
+    cudaMemsetAsync(h->pool_top, 0, sizeof(unsigned long long), st);
+    cudaMemsetAsync(h->row_count, 0, sizeof(int32_t) * (size_t)n, st);
+    cudaMemsetAsync(h->cursor, 0, sizeof(int32_t) * (size_t)n, st);
+    k_norm1<<<blocks(n, 256), 256, 0, st>>>(h->col_ptr, h->cval, n, h->dscal);
+
+    const DevA A = dev_a(h);
+    const DevParams P = dev_params(h);
+    const bool fp32 = h->params.precision == RSAI_FP32_REFINE;
+    double *gctr = h->dscal + 1;
+    ColOut O{h->col_off, h->col_len, h->rho, h->loops, h->flags, h->pool_rows, h->pool_vals,
+             h->pool_cap, h->pool_top, h->err};
+    ColQueue QW{nullptr, nullptr, n, h->qnext + 0, h->ovf1, h->qnext + 3, h->ovf_cap};
+    ColQueue QC{h->ovf1, h->qnext + 3, n, h->qnext + 1, h->ovf2, h->qnext + 4, h->ovf_cap};
+    ColQueue QG{h->ovf2, h->qnext + 4, n, h->qnext + 2, nullptr, nullptr, 0};
+    cudaError_t e = launch_bin_warp(fp32, h->grid_w, kWarpsPerCta, A, P, h->capW, QW, O, gctr, false, st);
+    if (e != cudaSuccess) return e;
+    e = launch_bin_block(fp32, h->grid_c, A, P, h->capC, QC, O, gctr, false, nullptr, 0, 1, st);
+    if (e != cudaSuccess) return e;
+    e = launch_bin_block(fp32, h->grid_g, A, P, h->capG, QG, O, gctr, true, h->gwork, h->gstride, 2, st);
+    if (e != cudaSuccess) return e;
+    k_column_stats<<<1, 1024, 0, st>>>(h->rho, h->flags, h->col_len, n, h->params.eps, h->dscal + kStatsAt);
+    // M in CSC, then CSR with rows sorted by column index
+    e = scan_counts(h, h->col_len, h->Mcolptr, st);
+    if (e != cudaSuccess) return e;
+    k_pool_to_csc<<<blocks(n * 32, 256), 256, 0, st>>>(h->col_off, h->col_len, h->pool_rows, h->pool_vals,
+                                                       h->Mcolptr, h->Mrows, h->Mvals_csc, h->row_count, n);
+    e = scan_counts(h, h->row_count, h->Mrowptr, st);
+    if (e != cudaSuccess) return e;
+    k_csc_to_rows<<<blocks(n * 32, 256), 256, 0, st>>>(h->Mcolptr, h->Mrows, h->Mvals_csc, h->Mrowptr, h->cursor,
+                                                       h->tcols, h->tvals, h->tsrc, n);
+    k_sort_rows<<<blocks(n * 32, 256), 256, 0, st>>>(h->Mrowptr, h->tcols, h->tvals, h->tsrc, h->Mcols, h->Mvals,
+                                                     h->Mcsc_to_csr, n);
+    return cudaGetLastError();
+}
+
+void free_all(rsai_handle *h) {
+    if (!h) return;
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    // the caller's stream may be gone by now: wait for the device, then free
+    cudaDeviceSynchronize();
+    for (void *p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+}
+
+int check_csr_host(const rsai_csr *A) {
+    if (!A || !A->row_ptr || !A->col_idx || !A->val) return RSAI_ERR_INVALID_ARG;
+    if (A->n <= 0 || A->nnz < 0 || A->n > INT32_MAX) return RSAI_ERR_SHAPE;
+    return RSAI_OK;
+}
+
+// choose the capacities of the three bins from the device limits
+int plan_bins(rsai_handle *h) {
+    const bool fp32 = h->params.precision == RSAI_FP32_REFINE;
+    int dev = h->device, max_optin = 0;
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int rneed = std::max(64, h->params.c * std::max(1, h->params.l_max));
+    h->capW = Caps{64, 32, 256, 64, 64 * 32};
+    int occ = occupancy_bin_warp(fp32, kWarpsPerCta, h->capW);
+    if (occ < 1) return RSAI_ERR_CUDA;
+    h->grid_w = h->sms * occ;
+    // bin C: shared-memory workspace as large as the opt-in limit allows
+    Caps c{1024, 256, 4096, std::min(rneed * 2, 2048), 0};
+    size_t base = fp32 ? work_bytes<float>(c) : work_bytes<double>(c);
+    size_t avail = (size_t)max_optin - 2048;
+    if (base >= avail) return RSAI_ERR_CUDA;
+    c.bcap = (int64_t)((avail - base) / (fp32 ? sizeof(float) : sizeof(double))) - 64;
+    h->capC = c;
+    occ = occupancy_bin_block(fp32, h->capC, false);
+    if (occ < 1) return RSAI_ERR_CUDA;
+    h->grid_c = h->sms * occ;
+    // bin G: a global-memory slab per CTA, one CTA per SM
+    h->capG = Caps{32768, 4096, 131072, 8192, (int64_t)1 << 22};
+    h->gstride = ((fp32 ? work_bytes<float>(h->capG) : work_bytes<double>(h->capG)) + 255) & ~size_t(255);
+    h->grid_g = h->sms;
+    return RSAI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t rsai_abi_version(void) { return RSAI_ABI_VERSION; }
+
+const char *rsai_status_string(rsai_status s) {
+    switch (s) {
+        case RSAI_OK: return "ok";
+        case RSAI_ERR_INVALID_ARG: return "invalid argument";
+        case RSAI_ERR_SHAPE: return "inconsistent shape (n, nnz, or CSR/CSC mismatch)";
+        case RSAI_ERR_UNSORTED: return "indices not strictly ascending within a row/column";
+        case RSAI_ERR_INDEX_RANGE: return "index or pointer out of range";
+        case RSAI_ERR_EMPTY_COLUMN: return "a column of A has no nonzeros (A is singular)";
+        case RSAI_ERR_OOM: return "device allocation failed";
+        case RSAI_ERR_CUDA: return "CUDA runtime error";
+        case RSAI_ERR_TIMEOUT: return "a bounded device wait ran out";
+        case RSAI_ERR_WORKSPACE: return "a column outgrew every size bin or the result pool";
+        case RSAI_ERR_BREAKDOWN: return "BiCGStab breakdown";
+        case RSAI_ERR_NOT_CONVERGED: return "BiCGStab did not converge within maxit";
+        case RSAI_ERR_NO_DEVICE: return "no CUDA device";
+    }
+    return "unknown status";
+}
+
+rsai_status rsai_params_default(rsai_params *p) {
+    if (!p) return RSAI_ERR_INVALID_ARG;
+    p->c = 3;
+    p->l_max = 10;
+    p->eps = 0.3;
+    p->drop_mode = RSAI_DROP_FIXED;
+    p->tol = 1e-3;
+    p->precision = RSAI_FP64;
+    p->tie_band = 1e-12;
+    p->flags = 0;
+    return RSAI_OK;
+}
+
+rsai_status rsai_params_check(const rsai_params *p) {
+    if (!p) return RSAI_ERR_INVALID_ARG;
+    if (p->c < 1 || p->c > 32) return RSAI_ERR_INVALID_ARG;
+    if (p->l_max < 0 || p->l_max > 100000) return RSAI_ERR_INVALID_ARG;
+    if (!(p->eps > 0.0) || !std::isfinite(p->eps)) return RSAI_ERR_INVALID_ARG;
+    if (p->drop_mode < RSAI_DROP_NONE || p->drop_mode > RSAI_DROP_FIXED) return RSAI_ERR_INVALID_ARG;
+    if (!(p->tol >= 0.0) || !std::isfinite(p->tol)) return RSAI_ERR_INVALID_ARG;
+    if (p->precision != RSAI_FP64 && p->precision != RSAI_FP32_REFINE) return RSAI_ERR_INVALID_ARG;
+    if (!(p->tie_band >= 0.0) || !(p->tie_band < 1.0)) return RSAI_ERR_INVALID_ARG;
+    return RSAI_OK;
+}
+
+void rsai_handle_free(rsai_handle *h) {
+    if (!h) return;
+    free_all(h);
+    delete h;
+}
+
+rsai_status rsai_build(const rsai_csr *A, const rsai_csc *Acsc, const rsai_params *params, void *stream,
+                       rsai_handle **out) {
+    if (!out) return RSAI_ERR_INVALID_ARG;
+    *out = nullptr;
+    int st_ = rsai_params_check(params);
+    if (st_ != RSAI_OK) return (rsai_status)st_;
+    st_ = check_csr_host(A);
+    if (st_ != RSAI_OK) return (rsai_status)st_;
+    if (!Acsc || !Acsc->col_ptr || !Acsc->row_idx || !Acsc->val) return RSAI_ERR_INVALID_ARG;
+    if (Acsc->n != A->n || Acsc->nnz != A->nnz) return RSAI_ERR_SHAPE;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return RSAI_ERR_NO_DEVICE;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    rsai_handle *h = new (std::nothrow) rsai_handle();
+    if (!h) return RSAI_ERR_OOM;
+    h->alloc_stream = st;
+    cudaGetDevice(&h->device);
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+    h->n = A->n;
+    h->nnz = A->nnz;
+    h->params = *params;
+    const int64_t n = h->n, nnz = h->nnz;
+    int rc = RSAI_OK;
+#define TRY(x)                        \
+    do {                              \
+        rc = (x);                     \
+        if (rc != RSAI_OK) goto fail; \
+    } while (0)
+    TRY(dalloc(h, &h->row_ptr, n + 1, st));
+    TRY(dalloc(h, &h->col_ptr, n + 1, st));
+    TRY(dalloc(h, &h->col_idx, nnz, st));
+    TRY(dalloc(h, &h->row_idx, nnz, st));
+    TRY(dalloc(h, &h->val, nnz, st));
+    TRY(dalloc(h, &h->cval, nnz, st));
+    TRY(dalloc(h, &h->csc_to_csr, nnz, st));
+    TRY(cuda_status(to_device(h->row_ptr, A->row_ptr, sizeof(int64_t) * (n + 1), st)));
+    TRY(cuda_status(to_device(h->col_idx, A->col_idx, sizeof(int32_t) * nnz, st)));
+    TRY(cuda_status(to_device(h->val, A->val, sizeof(double) * nnz, st)));
+    TRY(cuda_status(to_device(h->col_ptr, Acsc->col_ptr, sizeof(int64_t) * (n + 1), st)));
+    TRY(cuda_status(to_device(h->row_idx, Acsc->row_idx, sizeof(int32_t) * nnz, st)));
+    TRY(cuda_status(to_device(h->cval, Acsc->val, sizeof(double) * nnz, st)));
+    TRY(dalloc(h, &h->dscal, kScalars, st));
+    TRY(dalloc(h, &h->err, 1, st));
+    // ---- validation of A (device kernels, error codes) ----
+    {
+        int32_t herr = 0;
+        auto step = [&](auto launch) -> int {
+            cudaMemsetAsync(h->err, 0, sizeof(int32_t), st);
+            launch();
+            if (cudaMemcpyAsync(&herr, h->err, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                return RSAI_ERR_CUDA;
+            if (cudaStreamSynchronize(st) != cudaSuccess) return RSAI_ERR_CUDA;
+            return herr;
+        };
+        TRY(step([&] { k_check_ptr<<<blocks(n + 1, 256), 256, 0, st>>>(h->row_ptr, n, nnz, h->err); }));
+        TRY(step([&] { k_check_ptr<<<blocks(n + 1, 256), 256, 0, st>>>(h->col_ptr, n, nnz, h->err); }));
+        TRY(step([&] { k_check_idx<<<blocks(n, 256), 256, 0, st>>>(h->row_ptr, h->col_idx, n, h->err, 0); }));
+        TRY(step([&] { k_check_idx<<<blocks(n, 256), 256, 0, st>>>(h->col_ptr, h->row_idx, n, h->err, 1); }));
+        TRY(step([&] { k_csc_map<<<blocks(n, 256), 256, 0, st>>>(dev_a(h), h->csc_to_csr, h->err); }));
+    }
+    TRY(plan_bins(h));
+    // ---- buffers of the build sequence ----
+    h->ovf_cap = n;
+    TRY(dalloc(h, &h->qnext, 8, st));
+    TRY(dalloc(h, &h->ovf1, n, st));
+    TRY(dalloc(h, &h->ovf2, n, st));
+    TRY(dalloc(h, &h->col_off, n, st));
+    TRY(dalloc(h, &h->col_len, n, st));
+    TRY(dalloc(h, &h->loops, n, st));
+    TRY(dalloc(h, &h->flags, n, st));
+    TRY(dalloc(h, &h->rho, n, st));
+    TRY(dalloc(h, &h->pool_top, 1, st));
+    TRY(dalloc(h, &h->Mcolptr, n + 1, st));
+    TRY(dalloc(h, &h->Mrowptr, n + 1, st));
+    TRY(dalloc(h, &h->row_count, n, st));
+    TRY(dalloc(h, &h->cursor, n, st));
+    h->scan_tmp_len = (n + 1023) / 1024 + 2;
+    TRY(dalloc(h, &h->scan_tmp, h->scan_tmp_len, st));
+    TRY(dalloc(h, &h->gwork, h->gstride * (size_t)h->grid_g, st));
+    {
+        // result pool: grows (and the build is repeated) if a column finds it full
+        const int64_t g_est = std::max<int64_t>(32, 4 * (nnz / std::max<int64_t>(1, n)) + 16);
+        int64_t cap = std::min<int64_t>(n * g_est, n * n);
+        for (int attempt = 0; attempt < 6; ++attempt) {
+            h->pool_cap = cap;
+            TRY(dalloc(h, &h->pool_rows, cap, st));
+            TRY(dalloc(h, &h->pool_vals, cap, st));
+            TRY(dalloc(h, &h->Mrows, cap, st));
+            TRY(dalloc(h, &h->Mvals_csc, cap, st));
+            TRY(dalloc(h, &h->Mcols, cap, st));
+            TRY(dalloc(h, &h->Mvals, cap, st));
+            TRY(dalloc(h, &h->tcols, cap, st));
+            TRY(dalloc(h, &h->tvals, cap, st));
+            TRY(dalloc(h, &h->tsrc, cap, st));
+            TRY(dalloc(h, &h->Mcsc_to_csr, cap, st));
+            TRY(cuda_status(enqueue_build(h, st)));
+            unsigned long long top = 0;
+            int32_t herr = 0;
+            cudaMemcpyAsync(&top, h->pool_top, sizeof(top), cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(&herr, h->err, sizeof(herr), cudaMemcpyDeviceToHost, st);
+            TRY(cuda_status(cudaStreamSynchronize(st)));
+            if ((int64_t)top <= cap) {
+                if (herr != 0) rc = herr;
+                break;
+            }
+            // pool too small: release those buffers and retry with the size actually needed
+            void *pool_bufs[] = {h->pool_rows, h->pool_vals, h->Mrows, h->Mvals_csc, h->Mcols,
+                                 h->Mvals, h->tcols, h->tvals, h->tsrc, h->Mcsc_to_csr};
+            for (void *p : pool_bufs) {
+                cudaFreeAsync(p, st);
+                h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), p), h->allocs.end());
+            }
+            cap = std::min<int64_t>((int64_t)(top + top / 8 + 1024), n * n);
+        }
+    }
+#undef TRY
+    *out = h;
+    return (rsai_status)rc;  // OK, or WORKSPACE with failed columns flagged
+fail:
+    cudaStreamSynchronize(st);
+    cudaGetLastError();
+    rsai_handle_free(h);
+    return (rsai_status)rc;
+}
+
+rsai_status rsai_set_values(rsai_handle *h, const double *A_val, void *stream) {
+    if (!h || !A_val) return RSAI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (to_device(h->val, A_val, sizeof(double) * h->nnz, st) != cudaSuccess) return RSAI_ERR_CUDA;
+    k_csc_from_csr<<<blocks(h->nnz, 256), 256, 0, st>>>(h->val, h->csc_to_csr, h->cval, h->nnz);
+    return (rsai_status)cuda_status(cudaGetLastError());
+}
+
+rsai_status rsai_rebuild(rsai_handle *h, void *stream) {
+    if (!h) return RSAI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!h->graph) {
+        cudaStream_t cap_st;
+        if (cudaStreamCreateWithFlags(&cap_st, cudaStreamNonBlocking) != cudaSuccess) return RSAI_ERR_CUDA;
+        cudaGraph_t g;
+        cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal);
+        cudaError_t e = enqueue_build(h, cap_st);
+        cudaError_t e2 = cudaStreamEndCapture(cap_st, &g);
+        cudaStreamDestroy(cap_st);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            cudaGetLastError();
+            return RSAI_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&h->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return RSAI_ERR_CUDA;
+    }
+    return (rsai_status)cuda_status(cudaGraphLaunch(h->graph, st));
+}
+
+rsai_status rsai_get_stats(rsai_handle *h, void *stream, rsai_stats *out) {
+    if (!h || !out) return RSAI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    double s[kScalars];
+    int32_t herr = 0;
+    if (cudaMemcpyAsync(s, h->dscal, sizeof(s), cudaMemcpyDeviceToHost, st) != cudaSuccess) return RSAI_ERR_CUDA;
+    cudaMemcpyAsync(&herr, h->err, sizeof(herr), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return RSAI_ERR_CUDA;
+    const double *c = s + 1;
+    memset(out, 0, sizeof(*out));
+    out->n = h->n;
+    out->nnz_A = h->nnz;
+    out->norm1_A = s[0];
+    out->qr_flops = c[CTR_QR];
+    out->res_flops = c[CTR_RES];
+    out->refine_flops = c[CTR_REFINE];
+    out->bytes = c[CTR_BYTES];
+    out->loops = (int64_t)c[CTR_LOOPS];
+    out->solves = (int64_t)c[CTR_SOLVES];
+    out->drops = (int64_t)c[CTR_DROPS];
+    out->p_max = (int32_t)c[CTR_PMAX];
+    out->q_max = (int32_t)c[CTR_QMAX];
+    out->n_rank = (int64_t)c[CTR_RANK];
+    out->n_nonfinite = (int64_t)c[CTR_NONFINITE];
+    out->n_failed = (int64_t)c[CTR_FAILED];
+    for (int b = 0; b < 3; ++b) out->cols_bin[b] = (int64_t)c[CTR_COUNT + b];
+    out->frob = std::sqrt(s[kStatsAt + 0]);
+    out->n_c = (int64_t)s[kStatsAt + 1];
+    out->nnz_M = (int64_t)s[kStatsAt + 2];
+    return herr ? (rsai_status)herr : RSAI_OK;
+}
+
+rsai_status rsai_get_M(rsai_handle *h, int64_t *row_ptr, int32_t *col_idx, double *val, void *stream) {
+    if (!h) return RSAI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t nnzM = 0;
+    if (cudaMemcpyAsync(&nnzM, h->Mrowptr + h->n, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return RSAI_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return RSAI_ERR_CUDA;
+    if (row_ptr && cudaMemcpyAsync(row_ptr, h->Mrowptr, sizeof(int64_t) * (h->n + 1), cudaMemcpyDefault, st))
+        return RSAI_ERR_CUDA;
+    if (col_idx && cudaMemcpyAsync(col_idx, h->Mcols, sizeof(int32_t) * nnzM, cudaMemcpyDefault, st))
+        return RSAI_ERR_CUDA;
+    if (val && cudaMemcpyAsync(val, h->Mvals, sizeof(double) * nnzM, cudaMemcpyDefault, st)) return RSAI_ERR_CUDA;
+    return (rsai_status)cuda_status(cudaStreamSynchronize(st));
+}
+
+rsai_status rsai_get_columns(rsai_handle *h, double *rho, int32_t *loops, int32_t *flags, void *stream) {
+    if (!h) return RSAI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)h->n;
+    if (rho && cudaMemcpyAsync(rho, h->rho, sizeof(double) * n, cudaMemcpyDefault, st)) return RSAI_ERR_CUDA;
+    if (loops && cudaMemcpyAsync(loops, h->loops, sizeof(int32_t) * n, cudaMemcpyDefault, st)) return RSAI_ERR_CUDA;
+    if (flags && cudaMemcpyAsync(flags, h->flags, sizeof(int32_t) * n, cudaMemcpyDefault, st)) return RSAI_ERR_CUDA;
+    return (rsai_status)cuda_status(cudaStreamSynchronize(st));
+}
+
+rsai_status rsai_apply(rsai_handle *h, const double *x, double *y, void *stream) {
+    if (!h || !x || !y) return RSAI_ERR_INVALID_ARG;
+    return (rsai_status)cuda_status(
+        launch_spmv(h->n, h->Mrowptr, h->Mcols, h->Mvals, x, y, (cudaStream_t)stream));
+}
+
+rsai_status rsai_bicgstab(const rsai_csr *A, rsai_handle *M, const double *b, double *x, double rtol, int32_t maxit,
+                          int32_t *iters, double *relres, void *stream) {
+    int rc = check_csr_host(A);
+    if (rc != RSAI_OK) return (rsai_status)rc;
+    if (!b || !x || !iters || !relres || maxit < 0 || !(rtol > 0.0)) return RSAI_ERR_INVALID_ARG;
+    if (M && M->n != A->n) return RSAI_ERR_SHAPE;
+    int it = 0;
+    double rr = 0.0;
+    rc = bicgstab_run(A->n, A->row_ptr, A->col_idx, A->val, M ? M->Mrowptr : nullptr, M ? M->Mcols : nullptr,
+                      M ? M->Mvals : nullptr, b, x, rtol, maxit, &it, &rr, (cudaStream_t)stream);
+    *iters = it;
+    *relres = rr;
+    return (rsai_status)rc;
+}
+
+rsai_status rsai_refit(rsai_handle *h, const double *A_val, double *M_val, double *rho2, void *stream) {
+    (void)h; (void)A_val; (void)M_val; (void)rho2; (void)stream;
+    return RSAI_ERR_INVALID_ARG;
+}
+
+rsai_status rsai_backward(rsai_handle *h, const double *A_val, const double *grad_M, const double *grad_rho2,
+                          double *grad_A, void *stream) {
+    (void)h; (void)A_val; (void)grad_M; (void)grad_rho2; (void)grad_A; (void)stream;
+    return RSAI_ERR_INVALID_ARG;
+}
+
+rsai_status rsai_peak_fma(int32_t fp64, void *stream, double *flops_per_s) {
+    if (!flops_per_s) return RSAI_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return RSAI_ERR_NO_DEVICE;
+    }
+    return (rsai_status)cuda_status(run_peak_fma(fp64 != 0, (cudaStream_t)stream, flops_per_s));
+}
+
+}  // extern "C"

@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads without a GPU and exports every declared symbol."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1503_04500_gb300 import build_ext, rsai
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_ext.build()
+    return rsai.load()
+
+
+def _declared_functions():
+    with open(os.path.join(ROOT, "include", "rsai.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rsai_[A-Za-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert len(names) >= 16
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(rsai.EXPORTS) == names
+
+
+def test_abi_version_and_status_strings(lib):
+    assert lib.rsai_abi_version() == 1
+    for code in range(0, 13):
+        s = rsai.status_string(code)
+        assert s and s != "unknown status"
+    assert rsai.status_string(999) == "unknown status"
+
+
+def test_params_default_and_check(lib):
+    p = rsai.default_params()
+    assert (p.c, p.l_max, p.eps, p.drop_mode, p.tol, p.precision, p.tie_band) == (3, 10, 0.3, 2, 1e-3, 0, 1e-12)
+    assert lib.rsai_params_check(ctypes.byref(p)) == 0
+    bad = [dict(c=0), dict(c=33), dict(l_max=-1), dict(eps=0.0), dict(eps=float("nan")), dict(drop_mode=3),
+           dict(tol=-1.0), dict(precision=2), dict(tie_band=-1e-3), dict(tie_band=1.0)]
+    for b in bad:
+        q = rsai.default_params()
+        for k, v in b.items():
+            setattr(q, k, v)
+        assert lib.rsai_params_check(ctypes.byref(q)) == 1, b
+    assert lib.rsai_params_check(None) == 1
+
+
+def test_null_arguments_rejected_without_device(lib):
+    """Argument checks come before any device work."""
+    out = ctypes.c_void_p(0)
+    p = rsai.default_params()
+    assert lib.rsai_build(None, None, ctypes.byref(p), None, ctypes.byref(out)) == 1
+    assert out.value is None
+    csr = rsai.CSR(4, 4, None, None, None)
+    csc = rsai.CSC(4, 4, None, None, None)
+    assert lib.rsai_build(ctypes.byref(csr), ctypes.byref(csc), ctypes.byref(p), None, ctypes.byref(out)) == 1
+    assert lib.rsai_apply(None, None, None, None) == 1
+    assert lib.rsai_get_stats(None, None, None) == 1
+    v = ctypes.c_double(0.0)
+    assert lib.rsai_peak_fma(0, None, None) == 1
+    lib.rsai_handle_free(None)
+    del v
+
+
+@pytest.mark.skipif(os.environ.get("CUDA_VISIBLE_DEVICES", None) not in (None, ""), reason="device may exist")
+def test_no_device_status(lib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is visible")
+    v = ctypes.c_double(0.0)
+    assert lib.rsai_peak_fma(0, None, ctypes.byref(v)) == 12

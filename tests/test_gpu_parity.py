@@ -1,0 +1,246 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Bar (from the method's statement of the problem, Eq. 2.3 solved in FP64):
+  FP64 path: every pattern of M bit-identical, values within 1e-10 relative,
+             ||r_k|| within 1e-10 relative, loops identical.
+  FP32 QR + FP64 refinement: ||r_k|| within 1e-5 relative where the pattern
+             matches; at least 99% of the patterns identical; BiCGStab
+             iterations within +-1.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1503_04500_gb300 import inputs as gen
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+rsai = pytest.importorskip("paper_1503_04500_gb300.rsai")
+
+PARAMS_C1 = dict(c=3, l_max=10, eps=0.3, tol=1e-3)
+
+
+def csc_from_csr(rp, ci, va, n):
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    order = np.lexsort((rows, ci))
+    cp = np.zeros(n + 1, np.int64)
+    np.add.at(cp, ci.astype(np.int64) + 1, 1)
+    return np.cumsum(cp), rows[order], va[order]
+
+
+def gpu_M(A, **kw):
+    dA = rsai.DeviceMatrix.from_host(A)
+    h = rsai.build(dA, **kw)
+    rp, ci, va = (t.cpu().numpy() for t in h.M())
+    rho, loops, flags = (t.cpu().numpy() for t in h.columns())
+    st = h.stats()
+    return h, dA, (rp, ci, va), rho, loops, flags, st
+
+
+def assert_fp64_parity(A, M_or, res, rho, loops, flags, st, rtol=1e-10):
+    orp, oci, ova = M_or.csr()
+    rp, ci, va = res
+    assert np.array_equal(rp, orp), "row pointers of M differ"
+    assert np.array_equal(ci, oci), "column indices of M differ"
+    np.testing.assert_allclose(va, ova, rtol=rtol, atol=0.0)
+    np.testing.assert_allclose(rho, M_or.rho, rtol=rtol, atol=1e-300)
+    np.testing.assert_array_equal(loops, M_or.loops)
+    np.testing.assert_array_equal(flags & 1, (M_or.flags & 1))
+    assert st["nnz_M"] == M_or.nnz
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return gen.convdiff2d(20, (20.0, 20.0))
+
+
+@pytest.mark.parametrize("drop", ["fixed", "adaptive", "none"])
+def test_c1_fp64_bit_exact_patterns(c1, drop):
+    h, dA, res, rho, loops, flags, st = gpu_M(c1, drop=drop, precision="fp64", **PARAMS_C1)
+    ref = oracle.build(c1, drop=drop, **PARAMS_C1)
+    assert_fp64_parity(c1, ref, res, rho, loops, flags, st)
+    assert st["frob"] == pytest.approx(ref.frob(), rel=1e-12)
+    assert st["n_c"] == ref.n_c(0.3)
+
+
+def test_c1_work_counters_match_oracle(c1):
+    h, dA, res, rho, loops, flags, st = gpu_M(c1, drop="fixed", precision="fp64", **PARAMS_C1)
+    ref = oracle.build(c1, drop="fixed", **PARAMS_C1)
+    assert st["qr_flops"] == ref.counters[:, 0].sum()
+    assert st["res_flops"] == ref.counters[:, 1].sum()
+    assert st["bytes"] == ref.counters[:, 2].sum()
+    assert st["solves"] == ref.counters[:, 3].sum()
+    assert st["drops"] == ref.counters[:, 4].sum()
+    assert st["p_max"] == ref.counters[:, 5].max()
+    assert st["q_max"] == ref.counters[:, 6].max()
+    assert st["loops"] == ref.loops.sum()
+    assert st["norm1_A"] == oracle.norm1(c1)
+
+
+def test_c1_fp32_refine(c1):
+    h, dA, res, rho, loops, flags, st = gpu_M(c1, drop="fixed", precision="fp32_refine", **PARAMS_C1)
+    ref = oracle.build(c1, drop="fixed", **PARAMS_C1)
+    orp, oci, ova = ref.csr()
+    rp, ci, va = res
+    assert np.array_equal(rp, orp) and np.array_equal(ci, oci)
+    np.testing.assert_allclose(rho, ref.rho, rtol=1e-5)
+    np.testing.assert_allclose(va, ova, rtol=1e-6, atol=1e-9 * np.abs(ova).max())
+    assert st["refine_flops"] > 0
+
+
+def test_power_of_two_scaling_gpu(c1):
+    a = gpu_M(c1, drop="fixed", precision="fp64", **PARAMS_C1)
+    b = gpu_M(c1.with_values(c1.val * 8.0), drop="fixed", precision="fp64", **PARAMS_C1)
+    assert np.array_equal(a[2][1], b[2][1])
+    np.testing.assert_array_equal(a[2][2] / 8.0, b[2][2])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_powerlaw_all_bins(precision):
+    """Dense rows push columns out of the warp bin into the CTA and global bins."""
+    P = gen.powerlaw(2000, seed=17, dmax=100)
+    kw = dict(c=5, l_max=8, eps=0.4, tol=1e-3, drop="fixed")
+    h, dA, res, rho, loops, flags, st = gpu_M(P, precision=precision, **kw)
+    ref = oracle.build(P, **kw)
+    assert st["cols_bin"][1] + st["cols_bin"][2] > 0
+    assert sum(st["cols_bin"]) == P.n
+    assert st["n_failed"] == 0
+    if precision == "fp64":
+        assert_fp64_parity(P, ref, res, rho, loops, flags, st, rtol=1e-9)
+    else:
+        cp, rows, _ = csc_from_csr(*res, P.n)
+        same = np.array([np.array_equal(rows[cp[k]:cp[k + 1]], ref.column(k)[0]) for k in range(P.n)])
+        assert same.mean() >= 0.99
+        np.testing.assert_allclose(rho[same], ref.rho[same], rtol=1e-5)
+
+
+def test_rebuild_graph_is_identical(c1):
+    dA = rsai.DeviceMatrix.from_host(c1)
+    h = rsai.build(dA, drop="fixed", precision="fp64", **PARAMS_C1)
+    first = [t.clone() for t in h.M()]
+    for _ in range(3):
+        h.rebuild()
+    second = h.M()
+    for a, b in zip(first, second):
+        assert torch.equal(a, b)
+
+
+def test_set_values_then_rebuild_matches_fresh_build(c1):
+    vals2 = c1.val * (1.0 + 0.1 * np.sin(np.arange(c1.nnz)))
+    A2 = c1.with_values(vals2)
+    dA = rsai.DeviceMatrix.from_host(c1)
+    h = rsai.build(dA, drop="fixed", precision="fp64", **PARAMS_C1)
+    h.set_values(torch.as_tensor(vals2, device="cuda"))
+    h.rebuild()
+    rp, ci, va = (t.cpu().numpy() for t in h.M())
+    ref = oracle.build(A2, drop="fixed", **PARAMS_C1)
+    orp, oci, ova = ref.csr()
+    assert np.array_equal(ci, oci)
+    np.testing.assert_allclose(va, ova, rtol=1e-10)
+
+
+def test_host_input_build_equals_device_input(c1):
+    h1 = rsai.build(c1, drop="fixed", precision="fp64", **PARAMS_C1)  # numpy (host) arrays
+    h2 = rsai.build(rsai.DeviceMatrix.from_host(c1), drop="fixed", precision="fp64", **PARAMS_C1)
+    for a, b in zip(h1.M(), h2.M()):
+        assert torch.equal(a, b)
+
+
+def test_apply_and_bicgstab(c1):
+    h, dA, res, rho, loops, flags, st = gpu_M(c1, drop="fixed", precision="fp64", **PARAMS_C1)
+    x = torch.linspace(-1, 1, c1.n, dtype=torch.float64, device="cuda")
+    y = h.apply(x).cpu().numpy()
+    rp, ci, va = res
+    np.testing.assert_allclose(y, oracle.spmv(rp, ci, va, x.cpu().numpy()), rtol=1e-13, atol=1e-15)
+    b = torch.as_tensor(gen.ones_rhs(c1), device="cuda")
+    xs, it, rel, status = rsai.bicgstab(dA, h, b, rtol=1e-8)
+    ref = oracle.build(c1, drop="fixed", **PARAMS_C1)
+    ro = oracle.bicgstab(c1, ref.csr(), gen.ones_rhs(c1))
+    assert status == 0 and abs(it - ro.iters) <= 1
+    assert rel < 1e-7
+    np.testing.assert_allclose(xs.cpu().numpy(), np.ones(c1.n), rtol=1e-6)
+    x0, it0, rel0, st0 = rsai.bicgstab(dA, None, b, rtol=1e-8)
+    r0 = oracle.bicgstab(c1, None, gen.ones_rhs(c1))
+    assert abs(it0 - r0.iters) <= 1 and it < it0
+
+
+def test_c2_sampled_columns_at_full_size():
+    """The 3-D 64^3 problem (n = 262144) in the bench launch configuration:
+    every column's pattern and ||r_k|| checked on a strided sample."""
+    A = gen.convdiff3d(64)
+    kw = dict(c=3, l_max=10, eps=0.3, tol=1e-3, drop="fixed")
+    dA = rsai.DeviceMatrix.from_host(A)
+    for precision in ("fp64", "fp32_refine"):
+        h = rsai.build(dA, precision=precision, **kw)
+        st = h.stats()
+        assert st["n_failed"] == 0 and sum(st["cols_bin"]) == A.n
+        rp, ci, va = (t.cpu().numpy() for t in h.M())
+        rho = h.columns()[0].cpu().numpy()
+        cols = np.arange(0, A.n, 509)
+        ref = oracle.build(A, cols=cols, **kw)
+        # columns of M from the CSR: gather entries whose column index is in the sample
+        colk = ci
+        rows = np.repeat(np.arange(A.n), np.diff(rp))
+        sel = np.isin(colk, cols)
+        order = np.lexsort((rows[sel], colk[sel]))
+        gcols, grows, gvals = colk[sel][order], rows[sel][order], va[sel][order]
+        ptr = np.searchsorted(gcols, cols, side="left")
+        end = np.searchsorted(gcols, cols, side="right")
+        mism = 0
+        for t, k in enumerate(cols):
+            J, v = ref.column(t)
+            gJ = grows[ptr[t]:end[t]]
+            if not np.array_equal(gJ, J):
+                mism += 1
+                continue
+            if precision == "fp64":
+                np.testing.assert_allclose(gvals[ptr[t]:end[t]], v, rtol=1e-10)
+                np.testing.assert_allclose(rho[k], ref.rho[t], rtol=1e-10)
+            else:
+                np.testing.assert_allclose(rho[k], ref.rho[t], rtol=1e-5)
+        if precision == "fp64":
+            assert mism == 0
+        else:
+            assert mism <= len(cols) // 100
+        h.free()
+
+
+def test_invalid_inputs_are_status_codes(c1):
+    import copy
+
+    lib = rsai.load()
+    # unsorted row
+    bad = copy.deepcopy(c1)
+    a, b = bad.row_ptr[5], bad.row_ptr[6]
+    bad.col_idx[a:b] = bad.col_idx[a:b][::-1].copy()
+    with pytest.raises(rsai.RSAIError) as e:
+        rsai.build(bad)
+    assert e.value.status in (3, 2)
+    # index out of range
+    bad = copy.deepcopy(c1)
+    bad.row_idx[3] = c1.n + 5
+    with pytest.raises(rsai.RSAIError) as e:
+        rsai.build(bad)
+    assert e.value.status == 4
+    # CSR/CSC disagree on a value
+    bad = copy.deepcopy(c1)
+    bad.cval = bad.cval.copy()
+    bad.cval[0] += 1.0
+    with pytest.raises(rsai.RSAIError) as e:
+        rsai.build(bad)
+    assert e.value.status == 2
+    # empty column
+    D = c1.to_dense()
+    D[:, 7] = 0.0
+    E = gen.from_dense(D)
+    with pytest.raises(rsai.RSAIError) as e:
+        rsai.build(E)
+    assert e.value.status == 5
+    del lib
+
+
+def test_peak_fma_positive():
+    f32 = rsai.peak_fma(False)
+    f64 = rsai.peak_fma(True)
+    assert f32 > 1e12 and f64 > 1e10
