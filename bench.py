@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark of the RSAI(tol) build on GB300: M-columns/s at matched ||AM-I||_F.
+
+Workload: 3-D 7-point upwind convection-diffusion on 64^3 (n = 262144,
+nnz = 1,810,432), cell Peclet 5, c = 3 dominant rows per loop, l_max = 10,
+eps = 0.3, fixed drop tol = 1e-3 (on A/||A||_1).  A step is one whole build of
+M (||A||_1, every column's RSAI(tol) loop in the size bins, M to CSC and CSR)
+replayed as one CUDA graph on inputs already resident in HBM; L2 is flushed
+(256 MB write) between timed steps.
+
+`value` is the FP32-QR + FP64-refinement build; the plain FP64 build is timed
+beside it at the same ||AM-I||_F.  `e2e` times the public C-ABI call with
+pinned host buffers (copy in, validate, build, copy M out).  `--impl
+reference` times the FP64 CPU oracle on the host cores instead.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 (torchrun) every rank builds its own replica (weak scaling; the
+columns need no exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PARAMS = dict(c=3, l_max=10, eps=0.3, tol=1e-3, drop="fixed")
+METRIC = "RSAI M-columns/sec at matched ||AM-I||_F, FP32+refine vs FP64; bwd/fwd ratio"
+WORKLOAD = "convdiff3d_7pt_upwind_64^3_Pe5"
+KERNELS_PER_BUILD = 14  # norm1, 3 bins, column stats, 2 x 3 scan kernels, pool->CSC, CSC->rows, row sort
+# nominal CUDA-core rates (152 SMs): FP32 = 152 x 128 lanes x 2 flop x 2.07 GHz; FP64 as published for GB300
+PEAK_FP32_NOMINAL = 152 * 128 * 2 * 2.07e9
+PEAK_FP64_NOMINAL = 1.25e12
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while running; summary of the samples under load."""
+
+    def __init__(self, uuid: str | None):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.uuid = uuid
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            cmd = ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 10:
+                    continue
+                try:
+                    rows.append(dict(sm=float(p[1]), smmax=float(p[2]), util=float(p[4]), hw=p[6], hwt=p[7],
+                                     swt=p[8], swp=p[9]))
+                except ValueError:
+                    continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [r for r in rows if r["util"] > 0] or rows
+        reasons = set()
+        for r in load:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                              ("swp", "sw_power_cap")):
+                if r[key].lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in load), "sm_max_mhz": max(r["smmax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows), "samples_under_load": len(load)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1503_04500_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profiles(kernel: str, precision: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernels have not changed since."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except Exception:
+        return None
+    ent = data.get(f"{kernel}:{precision}")
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def run_oracle_sample(A, threads: int, stride: int):
+    import numpy as np
+
+    import oracle
+
+    cols = np.arange(0, A.n, stride, dtype=np.int64)
+    t0 = time.perf_counter()
+    M = oracle.build(A, cols=cols, threads=threads, **PARAMS)
+    dt = time.perf_counter() - t0
+    return len(cols), dt, M
+
+
+def reference_arm(args):
+    """The FP64 CPU oracle as it stands, on the host cores (rank 0 only)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1503_04500_gb300 import inputs
+
+    A = inputs.convdiff3d(64)
+    threads = os.cpu_count() or 1
+    stride = 2  # each step: every 2nd column (131072 columns)
+    for _ in range(args.warmup):
+        run_oracle_sample(A, threads, stride * 4)
+    times = []
+    ncols = 0
+    for _ in range(args.steps):
+        ncols, dt, _ = run_oracle_sample(A, threads, stride)
+        times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = ncols / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "columns/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, **PARAMS},
+        "cpu_baseline": {"value": value, "unit": "columns/s", "cores": threads, "kind": "oracle",
+                         "sample": f"every {stride}th column ({ncols} of {A.n}) per step"},
+        "e2e": {"value": value, "unit": "columns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_1503_04500_gb300 import inputs, rsai
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if pg is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
+
+    rsai.load()
+    A = inputs.convdiff3d(64)
+    dA = rsai.DeviceMatrix.from_host(A)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def timed(handle, steps):
+        st = torch.cuda.current_stream()
+        ms = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            handle.rebuild()
+            e1.record(st)
+            ms.append((e0, e1))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ms]
+
+    h32 = rsai.build(dA, precision="fp32_refine", **PARAMS)
+    h64 = rsai.build(dA, precision="fp64", **PARAMS)
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        h32.rebuild()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    barrier()
+    with ClockSampler(uuid) as clk:
+        barrier()
+        t_wall0 = time.perf_counter()
+        ms32 = timed(h32, args.steps)
+        barrier()
+        t_wall = time.perf_counter() - t_wall0
+    clocks = clk.summary()
+    dev_ms = max_over_ranks(sum(ms32)) / args.steps
+    s32 = h32.stats()
+    # FP64 path at the same parameters (the comparison of the metric)
+    k64 = max(3, args.steps // 5)
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        h64.rebuild()
+    barrier()
+    ms64 = timed(h64, k64)
+    barrier()
+    dev_ms64 = max_over_ranks(sum(ms64)) / k64
+    s64 = h64.stats()
+
+    # roofline of the dominant kernel (the warp bin): live per-phase CUDA events
+    phases32, phases64 = [], []
+    for _ in range(5):
+        flush.fill_(1.0)
+        phases32.append(h32.phase_times())
+        flush.fill_(1.0)
+        phases64.append(h64.phase_times())
+    ph32 = {k: statistics.median(p[k] for p in phases32) for k in phases32[0]}
+    ph64 = {k: statistics.median(p[k] for p in phases64) for k in phases64[0]}
+    f32_meas = rsai.peak_fma(False)
+    f64_meas = rsai.peak_fma(True)
+
+    def roofline(stats, ph, precision):
+        t = ph["bin_warp"] / 1e3
+        all_in_w = stats["cols_bin"][0] == stats["n"]
+        if precision == "fp32_refine":
+            F32 = stats["qr_flops"] + stats["refine_flops"]
+            F64 = stats["res_flops"] + stats["refine_flops_f64"]
+        else:
+            F32 = 0.0
+            F64 = stats["qr_flops"] + stats["res_flops"]
+        t32, t64 = F32 / PEAK_FP32_NOMINAL, F64 / PEAK_FP64_NOMINAL
+        pipe = "fp32" if t32 >= t64 else "fp64"
+        F, P = (F32, PEAK_FP32_NOMINAL) if pipe == "fp32" else (F64, PEAK_FP64_NOMINAL)
+        return {
+            "bound": "alu", "pipe": pipe, "kernel": f"k_bin_warp<{'float' if precision != 'fp64' else 'double'}>",
+            "achieved": F / t / 1e12, "peak": P / 1e12, "unit": "TFLOP/s", "frac": (F / t) / P,
+            "traffic": traffic_from_profiles("k_bin_warp", precision),
+            "peak_source": "derived from unit counts and max SM clock (FP32) / published GB300 FP64 rate",
+            "peak_measured_fma_chain": (f32_meas if pipe == "fp32" else f64_meas) / 1e12,
+            "launch_ms": ph["bin_warp"], "flops_fp32": F32, "flops_fp64": F64,
+            "t_roof_ms": 1e3 * max(t32, t64, stats["bytes"] / 6699.2e9), "all_columns_in_kernel": all_in_w,
+            "algorithmic_bytes": stats["bytes"],
+        }
+
+    roof32 = roofline(s32, ph32, "fp32_refine")
+    roof64 = roofline(s64, ph64, "fp64")
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a, dtype=dt)).pin_memory()  # noqa: E731
+        hA = rsai.DeviceMatrix(A.n, A.nnz, pin(A.row_ptr, np.int64), pin(A.col_idx, np.int32),
+                               pin(A.val, np.float64), pin(A.col_ptr, np.int64), pin(A.row_idx, np.int32),
+                               pin(A.cval, np.float64))
+        cap = s32["nnz_M"] + 1
+        out = (torch.empty(A.n + 1, dtype=torch.int64).pin_memory(), torch.empty(cap, dtype=torch.int32).pin_memory(),
+               torch.empty(cap, dtype=torch.float64).pin_memory())
+        h2d = 2 * (8 * (A.n + 1) + 12 * A.nnz)
+        e2e_t = []
+        d2h = 0
+        for i in range(args.e2e_steps + 1):
+            barrier()
+            t0 = time.perf_counter()
+            h = rsai.build(hA, precision="fp32_refine", **PARAMS)
+            st = h.stats()
+            h.M_host(st["nnz_M"], out=out)
+            h.free()
+            t1 = time.perf_counter()
+            if i > 0:
+                e2e_t.append(t1 - t0)
+            d2h = 8 * (A.n + 1) + 12 * st["nnz_M"] + 200
+        e2e_s = max_over_ranks(sum(e2e_t) / len(e2e_t))
+        e2e = {"value": world * A.n / e2e_s, "unit": "columns/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        ncols, dt, Mo = run_oracle_sample(A, threads, 1)
+        cpu = {"value": ncols / dt, "unit": "columns/s", "cores": threads, "kind": "oracle",
+               "sample": f"all {ncols} columns of the workload, FP64, {threads} threads", "seconds": dt,
+               "frob_oracle": Mo.frob()}
+
+    value = world * A.n / (dev_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "columns/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64refine", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, **PARAMS, "precision": "fp32_refine",
+                   "l2": "flushed (256 MB write) between timed steps", "replicas": world},
+        "frob": s32["frob"], "nnz_M": s32["nnz_M"], "n_c": s32["n_c"],
+        "fp64": {"value": world * A.n / (dev_ms64 / 1e3), "ms_per_step": dev_ms64, "frob": s64["frob"],
+                 "nnz_M": s64["nnz_M"], "roofline": roof64, "phases_ms": ph64},
+        "frob_rel_diff_fp32r_vs_fp64": abs(s32["frob"] - s64["frob"]) / s64["frob"],
+        "speedup_fp32r_vs_fp64": dev_ms64 / dev_ms,
+        "bwd_fwd_ratio": None,
+        "roofline": roof32, "phases_ms": ph32,
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": KERNELS_PER_BUILD * args.steps,
+        "wall_s_timed_region": t_wall,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h32.free()
+    h64.free()
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -112,9 +112,10 @@ typedef struct {
     int64_t n_c;          /* columns with ||r_k|| > eps (Section 5, n_c) */
     double frob;          /* ||AM - I||_F = sqrt(sum_k ||r_k||^2) */
     double norm1_A;       /* ||A||_1 (Eq. 4.3) */
-    double qr_flops;      /* algorithmic QR + solve flops (paper's QR update) */
-    double res_flops;     /* algorithmic FP64 residual flops */
-    double refine_flops;  /* FP32_REFINE only: algorithmic refinement flops */
+    double qr_flops;      /* algorithmic QR + solve flops (paper's QR update), in the QR precision */
+    double res_flops;     /* algorithmic FP64 residual flops (Eq. 2.4) */
+    double refine_flops;  /* FP32_REFINE only: FP32 flops of the refinement solves */
+    double refine_flops_f64; /* FP32_REFINE only: FP64 flops of the refinement residuals */
     double bytes;         /* algorithmic bytes */
     int64_t loops;        /* sum over columns of the loops used */
     int64_t solves;       /* LS solves */
@@ -226,6 +227,25 @@ rsai_status rsai_backward(rsai_handle *h, const double *A_val, const double *gra
  */
 rsai_status rsai_bicgstab(const rsai_csr *A, rsai_handle *M, const double *b, double *x, double rtol,
                           int32_t maxit, int32_t *iters, double *relres, void *stream);
+
+/* Phases of the build sequence timed by rsai_build_phase_times. */
+enum {
+    RSAI_PHASE_SETUP = 0,   /* counters reset, ||A||_1 */
+    RSAI_PHASE_BIN_WARP,    /* columns on one warp each */
+    RSAI_PHASE_BIN_CTA,     /* columns on one CTA each, shared-memory workspace */
+    RSAI_PHASE_BIN_GLOBAL,  /* columns on one CTA each, global-memory workspace */
+    RSAI_PHASE_ASSEMBLE,    /* statistics, M to CSC and CSR */
+    RSAI_PHASE_COUNT
+};
+
+/*
+ * rsai_build_phase_times -- run the build sequence of rsai_rebuild once more,
+ * launched phase by phase (not as a graph) with a CUDA event between phases on
+ * `stream`, and write each phase's duration in milliseconds to
+ * ms[RSAI_PHASE_COUNT].  Synchronises the stream.  The result of the build is
+ * the same as rsai_rebuild's.
+ */
+rsai_status rsai_build_phase_times(rsai_handle *h, void *stream, double *ms);
 
 /* Release a handle and its device memory (NULL is a no-op). */
 void rsai_handle_free(rsai_handle *h);

@@ -135,6 +135,7 @@ __device__ void emit_or_forward(const Team &team, Column<Team, T> &col, int st, 
         w.ctr[CTR_QR] += col.c_qr;
         w.ctr[CTR_RES] += col.c_res;
         w.ctr[CTR_REFINE] += col.c_ref;
+        w.ctr[CTR_REFINE64] += col.c_ref64;
         w.ctr[CTR_BYTES] += col.c_bytes;
         w.ctr[CTR_LOOPS] += (double)col.l;
         w.ctr[CTR_SOLVES] += col.c_solves;

@@ -108,7 +108,7 @@ template <class Team, typename T> struct Column {
     int rank_flag;
     double rho;
     // per-column work counters (committed only when the column finishes)
-    double c_qr, c_res, c_ref, c_bytes, c_solves, c_drops, c_pmax, c_qmax;
+    double c_qr, c_res, c_ref, c_ref64, c_bytes, c_solves, c_drops, c_pmax, c_qmax;
 
     __device__ Column(const Team &t, const DevA &a, const DevParams &pp, const Caps &c, Work<T> &ww, int32_t kk)
         : team(t), A(a), P(pp), cap(c), w(ww), k(kk) {}
@@ -243,7 +243,7 @@ template <class Team, typename T> struct Column {
         }
         rho = sqrt(team.sum(ss));
         double nnzJ = team.sum(cnt);
-        if (refine) c_ref += 2.0 * nnzJ + 2.0 * (double)s;
+        if (refine) c_ref64 += 2.0 * nnzJ + 2.0 * (double)s;
         else c_res += 2.0 * nnzJ + 2.0 * (double)s;
         team.sync();
     }
@@ -504,7 +504,7 @@ template <class Team, typename T> struct Column {
     __device__ int run() {
         const int me = team.rank();
         p = 1; q = 0; s = 0; nR = 0; l = 0; q0 = 0; p0 = 0; rank_flag = 0; rho = 0.0;
-        c_qr = c_res = c_ref = c_bytes = c_solves = c_drops = 0.0;
+        c_qr = c_res = c_ref = c_ref64 = c_bytes = c_solves = c_drops = 0.0;
         c_pmax = c_qmax = 0.0;
         if (me == 0) w.J[0] = k;
         team.sync();

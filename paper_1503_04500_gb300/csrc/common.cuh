@@ -35,7 +35,7 @@ struct DevParams {
 
 // Work counters of one team, summed into the global statistics at the end.
 enum Counter {
-    CTR_QR = 0, CTR_RES, CTR_REFINE, CTR_BYTES, CTR_LOOPS, CTR_SOLVES, CTR_DROPS,
+    CTR_QR = 0, CTR_RES, CTR_REFINE, CTR_REFINE64, CTR_BYTES, CTR_LOOPS, CTR_SOLVES, CTR_DROPS,
     CTR_PMAX, CTR_QMAX, CTR_COLS, CTR_RANK, CTR_NONFINITE, CTR_NC, CTR_FROB2, CTR_FAILED,
     CTR_COUNT
 };

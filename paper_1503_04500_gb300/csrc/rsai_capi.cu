@@ -115,8 +115,10 @@ cudaError_t scan_counts(rsai_handle *h, const int32_t *in, int64_t *out, cudaStr
 }
 
 // The build sequence: no allocation, no host synchronisation (capturable).
-cudaError_t enqueue_build(rsai_handle *h, cudaStream_t st) {
+// `ev` (optional, RSAI_PHASE_COUNT + 1 events) are recorded between phases.
+cudaError_t enqueue_build(rsai_handle *h, cudaStream_t st, cudaEvent_t *ev = nullptr) {
     const int64_t n = h->n;
+    if (ev) cudaEventRecord(ev[0], st);
     cudaMemsetAsync(h->dscal, 0, sizeof(double) * kScalars, st);
     cudaMemsetAsync(h->err, 0, sizeof(int32_t), st);
     cudaMemsetAsync(h->qnext, 0, sizeof(uint32_t) * 8, st);
@@ -134,12 +136,16 @@ cudaError_t enqueue_build(rsai_handle *h, cudaStream_t st) {
     ColQueue QW{nullptr, nullptr, n, h->qnext + 0, h->ovf1, h->qnext + 3, h->ovf_cap};
     ColQueue QC{h->ovf1, h->qnext + 3, n, h->qnext + 1, h->ovf2, h->qnext + 4, h->ovf_cap};
     ColQueue QG{h->ovf2, h->qnext + 4, n, h->qnext + 2, nullptr, nullptr, 0};
+    if (ev) cudaEventRecord(ev[1], st);
     cudaError_t e = launch_bin_warp(fp32, h->grid_w, kWarpsPerCta, A, P, h->capW, QW, O, gctr, false, st);
     if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[2], st);
     e = launch_bin_block(fp32, h->grid_c, A, P, h->capC, QC, O, gctr, false, nullptr, 0, 1, st);
     if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[3], st);
     e = launch_bin_block(fp32, h->grid_g, A, P, h->capG, QG, O, gctr, true, h->gwork, h->gstride, 2, st);
     if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[4], st);
     k_column_stats<<<1, 1024, 0, st>>>(h->rho, h->flags, h->col_len, n, h->params.eps, h->dscal + kStatsAt);
     // M in CSC, then CSR with rows sorted by column index
     e = scan_counts(h, h->col_len, h->Mcolptr, st);
@@ -152,6 +158,7 @@ cudaError_t enqueue_build(rsai_handle *h, cudaStream_t st) {
                                                        h->tcols, h->tvals, h->tsrc, n);
     k_sort_rows<<<blocks(n * 32, 256), 256, 0, st>>>(h->Mrowptr, h->tcols, h->tvals, h->tsrc, h->Mcols, h->Mvals,
                                                      h->Mcsc_to_csr, n);
+    if (ev) cudaEventRecord(ev[5], st);
     return cudaGetLastError();
 }
 
@@ -194,7 +201,7 @@ int plan_bins(rsai_handle *h) {
     // bin G: a global-memory slab per CTA, one CTA per SM
     h->capG = Caps{32768, 4096, 131072, 8192, (int64_t)1 << 22};
     h->gstride = ((fp32 ? work_bytes<float>(h->capG) : work_bytes<double>(h->capG)) + 255) & ~size_t(255);
-    h->grid_g = h->sms;
+    h->grid_g = std::min(h->sms, 8);  // grown after the first build if the tail needs it
     return RSAI_OK;
 }
 
@@ -372,6 +379,18 @@ rsai_status rsai_build(const rsai_csr *A, const rsai_csc *Acsc, const rsai_param
             cap = std::min<int64_t>((int64_t)(top + top / 8 + 1024), n * n);
         }
     }
+    {
+        // many columns in the global bin: give it one CTA per SM for later rebuilds
+        double cnt = 0.0;
+        cudaMemcpyAsync(&cnt, h->dscal + 1 + CTR_COUNT + 2, sizeof(double), cudaMemcpyDeviceToHost, st);
+        TRY(cuda_status(cudaStreamSynchronize(st)));
+        if (cnt > 16.0 * h->grid_g && h->grid_g < h->sms) {
+            cudaFreeAsync(h->gwork, st);
+            h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void *)h->gwork), h->allocs.end());
+            h->grid_g = h->sms;
+            TRY(dalloc(h, &h->gwork, h->gstride * (size_t)h->grid_g, st));
+        }
+    }
 #undef TRY
     *out = h;
     return (rsai_status)rc;  // OK, or WORKSPACE with failed columns flagged
@@ -428,6 +447,7 @@ rsai_status rsai_get_stats(rsai_handle *h, void *stream, rsai_stats *out) {
     out->qr_flops = c[CTR_QR];
     out->res_flops = c[CTR_RES];
     out->refine_flops = c[CTR_REFINE];
+    out->refine_flops_f64 = c[CTR_REFINE64];
     out->bytes = c[CTR_BYTES];
     out->loops = (int64_t)c[CTR_LOOPS];
     out->solves = (int64_t)c[CTR_SOLVES];
@@ -499,6 +519,24 @@ rsai_status rsai_backward(rsai_handle *h, const double *A_val, const double *gra
                           double *grad_A, void *stream) {
     (void)h; (void)A_val; (void)grad_M; (void)grad_rho2; (void)grad_A; (void)stream;
     return RSAI_ERR_INVALID_ARG;
+}
+
+rsai_status rsai_build_phase_times(rsai_handle *h, void *stream, double *ms) {
+    if (!h || !ms) return RSAI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t ev[RSAI_PHASE_COUNT + 1];
+    for (auto &e : ev) cudaEventCreate(&e);
+    cudaError_t e = enqueue_build(h, st, ev);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[RSAI_PHASE_COUNT]);
+    if (e == cudaSuccess) {
+        for (int i = 0; i < RSAI_PHASE_COUNT; ++i) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+            ms[i] = t;
+        }
+    }
+    for (auto &x : ev) cudaEventDestroy(x);
+    return (rsai_status)cuda_status(e);
 }
 
 rsai_status rsai_peak_fma(int32_t fp64, void *stream, double *flops_per_s) {

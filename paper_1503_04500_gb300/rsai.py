@@ -24,12 +24,13 @@ STATUS_NAMES = {
 DROP = {"none": 0, "adaptive": 1, "fixed": 2}
 PRECISION = {"fp64": 0, "fp32_refine": 1}
 COL_CONVERGED, COL_RANK, COL_NONFINITE, COL_FAILED = 1, 2, 4, 8
+PHASES = ("setup", "bin_warp", "bin_cta", "bin_global", "assemble")
 
 # every symbol include/rsai.h declares
 EXPORTS = [
     "rsai_abi_version", "rsai_status_string", "rsai_params_default", "rsai_params_check", "rsai_build",
     "rsai_rebuild", "rsai_set_values", "rsai_get_stats", "rsai_get_M", "rsai_get_columns", "rsai_refit",
-    "rsai_apply", "rsai_backward", "rsai_bicgstab", "rsai_handle_free", "rsai_peak_fma",
+    "rsai_apply", "rsai_backward", "rsai_bicgstab", "rsai_handle_free", "rsai_peak_fma", "rsai_build_phase_times",
 ]
 
 
@@ -59,6 +60,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz_A", ctypes.c_int64), ("nnz_M", ctypes.c_int64),
                 ("n_c", ctypes.c_int64), ("frob", ctypes.c_double), ("norm1_A", ctypes.c_double),
                 ("qr_flops", ctypes.c_double), ("res_flops", ctypes.c_double), ("refine_flops", ctypes.c_double),
+                ("refine_flops_f64", ctypes.c_double),
                 ("bytes", ctypes.c_double), ("loops", ctypes.c_int64), ("solves", ctypes.c_int64),
                 ("drops", ctypes.c_int64), ("p_max", ctypes.c_int32), ("q_max", ctypes.c_int32),
                 ("cols_bin", ctypes.c_int64 * 3), ("n_rank", ctypes.c_int64), ("n_nonfinite", ctypes.c_int64),
@@ -108,6 +110,7 @@ def load(build_if_missing: bool = False):
                                 ctypes.POINTER(f64), vp]),
         "rsai_handle_free": (None, [vp]),
         "rsai_peak_fma": (i32, [i32, vp, ctypes.POINTER(f64)]),
+        "rsai_build_phase_times": (i32, [vp, vp, ctypes.POINTER(f64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -252,6 +255,12 @@ class Handle:
 
     def rebuild(self, stream=None):
         _check(load().rsai_rebuild(self._h, _stream(stream)), "rsai_rebuild")
+
+    def phase_times(self, stream=None):
+        """Run the build once more phase by phase; per-phase milliseconds (CUDA events)."""
+        ms = (ctypes.c_double * 5)()
+        _check(load().rsai_build_phase_times(self._h, _stream(stream), ms), "rsai_build_phase_times")
+        return dict(zip(PHASES, list(ms)))
 
     def set_values(self, val, stream=None):
         _check(load().rsai_set_values(self._h, _ptr(val), _stream(stream)), "rsai_set_values")
