@@ -37,8 +37,8 @@
  *     its emitted pattern.
  *   - The residual lives on S = I u {k} (r(k) = -1 when k is not in I).
  *   - Ties: with v the c-th largest |r_i| of Cand and b = tie_band*||r||_inf,
- *     take every i with |r_i| - v > b, then fill up to c from
- *     {i : | |r_i| - v | <= b} by lowest index; "r_i != 0" means |r_i| > b.
+ *     take every i with |r_i| > v + b, then fill up to c from
+ *     {i : v - b <= |r_i| <= v + b} by lowest index; "r_i != 0" means |r_i| > b.
  *   - Algorithm 1 step 4 always excludes R (not only on a repeat); loops whose
  *     Jhat is empty still count toward l_max (step 6).
  *   - Rank: if |R_jj| <= q*u*||B||_F the column is flagged RANK and that
@@ -359,12 +359,13 @@ static void rsai_column(const omat *A, const oparams *P, int64_t k, ocol *out, o
         } else {
             qsort(cand, (size_t)nc, sizeof(keyed), cmp_dom);
             double v = cand[c - 1].a;
-            /* above the band: certainly among the top c; inside it: a tie */
-            for (int64_t t = 0; t < nc; ++t) if (cand[t].a - v > band) Rhat[nh++] = cand[t].i;
+            double hi = v + band, lo = v - band;
+            /* above the band: certainly among the top c; inside [lo, hi]: a tie */
+            for (int64_t t = 0; t < nc; ++t) if (cand[t].a > hi) Rhat[nh++] = cand[t].i;
             int64_t nt = 0;
             keyed *tie = malloc(sizeof(keyed) * (size_t)nc);
             for (int64_t t = 0; t < nc; ++t)
-                if (fabs(cand[t].a - v) <= band) tie[nt++] = cand[t];
+                if (cand[t].a >= lo && cand[t].a <= hi) tie[nt++] = cand[t];
             qsort(tie, (size_t)nt, sizeof(keyed), cmp_idx);
             for (int64_t t = 0; t < nt && nh < c; ++t) Rhat[nh++] = tie[t].i;
             free(tie);
