@@ -95,7 +95,7 @@ __device__ void emit_or_forward(const Team &team, Column<Team, T> &col, int st, 
             O.rho[k] = NAN;
             O.loops[k] = 0;
             O.flags[k] = RSAI_COL_FAILED;
-            w.ctr[CTR_FAILED] += 1.0;
+            w.ctr[CTR_FAILED] += 1;
             set_error(O.err, RSAI_ERR_WORKSPACE);
         }
         team.sync();
@@ -111,7 +111,7 @@ __device__ void emit_or_forward(const Team &team, Column<Team, T> &col, int st, 
             O.col_len[k] = 0;
             O.rho[k] = NAN;
             O.flags[k] = RSAI_COL_FAILED;
-            w.ctr[CTR_FAILED] += 1.0;
+            w.ctr[CTR_FAILED] += 1;
             set_error(O.err, RSAI_ERR_WORKSPACE);
         }
         team.sync();
@@ -121,9 +121,9 @@ __device__ void emit_or_forward(const Team &team, Column<Team, T> &col, int st, 
     for (int c = me; c < p; c += Team::SIZE) {
         O.pool_rows[off + c] = w.J[c];
         O.pool_vals[off + c] = w.m[c];
-        fin &= isfinite(w.m[c]) ? 1 : 0;
+        fin &= finite_bits(w.m[c]) ? 1 : 0;
     }
-    fin = (int)team.sum((double)(1 - fin)) == 0 && isfinite(col.rho);
+    fin = team.sum(1 - fin) == 0 && finite_bits(col.rho);
     if (me == 0) {
         int flags = (col.rho <= col.P.eps ? RSAI_COL_CONVERGED : 0) | (col.rank_flag ? RSAI_COL_RANK : 0) |
                     (fin ? 0 : RSAI_COL_NONFINITE);
@@ -137,14 +137,14 @@ __device__ void emit_or_forward(const Team &team, Column<Team, T> &col, int st, 
         w.ctr[CTR_REFINE] += col.c_ref;
         w.ctr[CTR_REFINE64] += col.c_ref64;
         w.ctr[CTR_BYTES] += col.c_bytes;
-        w.ctr[CTR_LOOPS] += (double)col.l;
+        w.ctr[CTR_LOOPS] += col.l;
         w.ctr[CTR_SOLVES] += col.c_solves;
         w.ctr[CTR_DROPS] += col.c_drops;
-        w.ctr[CTR_PMAX] = fmax(w.ctr[CTR_PMAX], col.c_pmax);
-        w.ctr[CTR_QMAX] = fmax(w.ctr[CTR_QMAX], col.c_qmax);
-        w.ctr[CTR_COLS] += 1.0;
-        w.ctr[CTR_RANK] += col.rank_flag ? 1.0 : 0.0;
-        w.ctr[CTR_NONFINITE] += fin ? 0.0 : 1.0;
+        w.ctr[CTR_PMAX] = max(w.ctr[CTR_PMAX], (long long)col.c_pmax);
+        w.ctr[CTR_QMAX] = max(w.ctr[CTR_QMAX], (long long)col.c_qmax);
+        w.ctr[CTR_COLS] += 1;
+        w.ctr[CTR_RANK] += col.rank_flag ? 1 : 0;
+        w.ctr[CTR_NONFINITE] += fin ? 0 : 1;
     }
     team.sync();
     (void)bin;
@@ -152,9 +152,9 @@ __device__ void emit_or_forward(const Team &team, Column<Team, T> &col, int st, 
 
 template <class Team, typename T>
 __device__ void run_queue(const Team &team, Work<T> &w, const DevA &A, const DevParams &P, const Caps &cap,
-                          const ColQueue &Q, const ColOut &O, double *gctr, bool last_bin, int bin) {
+                          const ColQueue &Q, const ColOut &O, unsigned long long *gctr, bool last_bin, int bin) {
     const int me = team.rank();
-    for (int i = me; i < CTR_COUNT; i += Team::SIZE) w.ctr[i] = 0.0;
+    for (int i = me; i < CTR_COUNT; i += Team::SIZE) w.ctr[i] = 0;
     team.sync();
     const int64_t nq = Q.count ? (int64_t)(*(volatile const uint32_t *)Q.count) : Q.n;
     for (;;) {
@@ -171,16 +171,17 @@ __device__ void run_queue(const Team &team, Work<T> &w, const DevA &A, const Dev
     if (me == 0) {
         for (int i = 0; i < CTR_COUNT; ++i) {
             if (i == CTR_PMAX || i == CTR_QMAX)
-                atomicMax((unsigned long long *)&gctr[i], (unsigned long long)__double_as_longlong(w.ctr[i]));
-            else if (w.ctr[i] != 0.0)
-                atomicAdd(&gctr[i], w.ctr[i]);
+                atomicMax(&gctr[i], (unsigned long long)w.ctr[i]);
+            else if (w.ctr[i] != 0)
+                atomicAdd(&gctr[i], (unsigned long long)w.ctr[i]);
         }
-        if (w.ctr[CTR_COLS] != 0.0) atomicAdd(&gctr[CTR_COUNT + bin], w.ctr[CTR_COLS]);
+        if (w.ctr[CTR_COLS] != 0) atomicAdd(&gctr[CTR_COUNT + bin], (unsigned long long)w.ctr[CTR_COLS]);
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_bin_warp(DevA A, DevParams P, Caps cap, ColQueue Q, ColOut O, double *gctr,
+__global__ void __launch_bounds__(128, 4) k_bin_warp(DevA A, DevParams P, Caps cap, ColQueue Q, ColOut O,
+                                                  unsigned long long *gctr,
                                                   int last_bin) {
     extern __shared__ __align__(16) char smem[];
     const int wid = threadIdx.x >> 5;
@@ -191,15 +192,16 @@ __global__ void __launch_bounds__(128) k_bin_warp(DevA A, DevParams P, Caps cap,
 }
 
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_bin_block(DevA A, DevParams P, Caps cap, ColQueue Q, ColOut O, double *gctr,
+__global__ void __launch_bounds__(NT, 1) k_bin_block(DevA A, DevParams P, Caps cap, ColQueue Q, ColOut O,
+                                                  unsigned long long *gctr,
                                                   int last_bin, char *gwork, size_t gstride, int bin) {
     extern __shared__ __align__(16) char smem[];
-    __shared__ double redd[NT / 32 + 1];
+    __shared__ unsigned long long red[NT / 32 + 1];
     __shared__ int redi[NT / 32 + 1];
     Work<T> w;
     if (gwork) w.carve(gwork + (size_t)blockIdx.x * gstride, cap);
     else w.carve(smem, cap);
-    BlockTeam<NT> team{redd, redi};
+    BlockTeam<NT> team{red, redi};
     run_queue(team, w, A, P, cap, Q, O, gctr, last_bin != 0, bin);
 }
 
@@ -207,31 +209,48 @@ __global__ void __launch_bounds__(NT) k_bin_block(DevA A, DevParams P, Caps cap,
 // statistics over the per-column outputs in a fixed order (deterministic)
 
 __global__ void k_column_stats(const double *rho, const int32_t *flags, const int32_t *len, int64_t n, double eps,
-                               double *out /* [frob2, n_c, nnz] */) {
-    __shared__ double s0[1024], s1[1024], s2[1024];
-    double a = 0.0, b = 0.0, c = 0.0;
-    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+                               double *partial /* [kStatBlocks] */, unsigned long long *counts /* [2] */) {
+    __shared__ double sh[256];
+    double a = 0.0;
+    unsigned long long nc = 0, nnz = 0;
+    for (int64_t k = blockIdx.x * 256LL + threadIdx.x; k < n; k += (int64_t)kStatBlocks * 256) {
         double r = rho[k];
-        if (!(flags[k] & RSAI_COL_FAILED)) {
-            a += r * r;
-            b += (r > eps) ? 1.0 : 0.0;
-        } else {
-            b += 1.0;
-        }
-        c += (double)len[k];
+        bool failed = flags[k] & RSAI_COL_FAILED;
+        if (!failed) a = fma(r, r, a);
+        nc += (failed || abskey(r) > abskey(eps)) ? 1 : 0;
+        nnz += (unsigned long long)len[k];
     }
-    s0[threadIdx.x] = a; s1[threadIdx.x] = b; s2[threadIdx.x] = c;
+    sh[threadIdx.x] = a;
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) {
-            s0[threadIdx.x] += s0[threadIdx.x + o];
-            s1[threadIdx.x] += s1[threadIdx.x + o];
-            s2[threadIdx.x] += s2[threadIdx.x + o];
-        }
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) { out[0] = s0[0]; out[1] = s1[0]; out[2] = s2[0]; }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nc += __shfl_xor_sync(0xffffffffu, nc, o);
+        nnz += __shfl_xor_sync(0xffffffffu, nnz, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&counts[0], nc);
+        atomicAdd(&counts[1], nnz);
+    }
 }
+
+__global__ void k_column_stats_final(const double *partial, double *frob2) {
+    __shared__ double sh[kStatBlocks];
+    sh[threadIdx.x] = partial[threadIdx.x];
+    __syncthreads();
+    for (int o = kStatBlocks / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *frob2 = sh[0];
+}
+
+// tol / ||A||_1, the threshold of the fixed drop rule, once per build
+__global__ void k_tau_fixed(const double *norm1, double tol, double *tau) { *tau = tol / *norm1; }
 
 // ---------------------------------------------------------------------------
 // exclusive scan of int32 counts into int64 offsets (three passes)
@@ -349,7 +368,8 @@ template size_t work_bytes<float>(const Caps &);
 template size_t work_bytes<double>(const Caps &);
 
 cudaError_t launch_bin_warp(bool fp32, int grid, int warps, const DevA &A, const DevParams &P, const Caps &cap,
-                            const ColQueue &Q, const ColOut &O, double *gctr, bool last, cudaStream_t st) {
+                            const ColQueue &Q, const ColOut &O, unsigned long long *gctr, bool last,
+                            cudaStream_t st) {
     size_t smem = fp32 ? warp_bin_smem<float>(cap, warps) : warp_bin_smem<double>(cap, warps);
     if (fp32) {
         cudaFuncSetAttribute(k_bin_warp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -362,7 +382,7 @@ cudaError_t launch_bin_warp(bool fp32, int grid, int warps, const DevA &A, const
 }
 
 cudaError_t launch_bin_block(bool fp32, int grid, const DevA &A, const DevParams &P, const Caps &cap,
-                             const ColQueue &Q, const ColOut &O, double *gctr, bool last, char *gwork,
+                             const ColQueue &Q, const ColOut &O, unsigned long long *gctr, bool last, char *gwork,
                              size_t gstride, int bin, cudaStream_t st) {
     size_t smem = gwork ? 0 : (fp32 ? Work<float>::bytes(cap) : Work<double>::bytes(cap));
     if (fp32) {

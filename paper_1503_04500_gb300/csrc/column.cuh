@@ -36,7 +36,8 @@ struct Caps {
 
 template <typename T> struct Work {
     T *B, *vhead, *vtv, *rhs;
-    double *m, *r, *ctr;
+    double *m, *r;
+    long long *ctr;
     int32_t *I, *S, *J, *Jn, *Rset, *buf, *buf2, *Rhat;
 
     __host__ __device__ static size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -47,7 +48,7 @@ template <typename T> struct Work {
         b += align16(sizeof(T) * (size_t)(c.qcap + 1));
         b += align16(sizeof(double) * (size_t)c.pcap);
         b += align16(sizeof(double) * (size_t)(c.qcap + 1));
-        b += align16(sizeof(double) * CTR_COUNT);
+        b += align16(sizeof(long long) * CTR_COUNT);
         b += align16(sizeof(int32_t) * (size_t)c.qcap);
         b += align16(sizeof(int32_t) * (size_t)(c.qcap + 1));
         b += 2 * align16(sizeof(int32_t) * (size_t)c.pcap);
@@ -64,7 +65,7 @@ template <typename T> struct Work {
         rhs = (T *)(base + o); o += align16(sizeof(T) * (size_t)(c.qcap + 1));
         m = (double *)(base + o); o += align16(sizeof(double) * (size_t)c.pcap);
         r = (double *)(base + o); o += align16(sizeof(double) * (size_t)(c.qcap + 1));
-        ctr = (double *)(base + o); o += align16(sizeof(double) * CTR_COUNT);
+        ctr = (long long *)(base + o); o += align16(sizeof(long long) * CTR_COUNT);
         I = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.qcap);
         S = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)(c.qcap + 1));
         J = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.pcap);
@@ -88,12 +89,12 @@ __host__ __device__ inline int next_pow2(int x) {
 // (q0,p0) (p0 = 0: from scratch): the reflectors of the old columns applied to
 // the new ones, Householder steps p0..p-1 on the stacked rows (norm, then every
 // trailing column and the right-hand side), and the back substitution.
-__device__ __forceinline__ double solve_flops(int64_t q0, int64_t p0, int64_t q, int64_t p) {
-    int64_t mm = p - p0;
-    int64_t f = 4 * mm * (p0 * q0 - p0 * (p0 - 1) / 2);
-    int64_t s2 = mm * (mm + 1) * (2 * mm + 1) / 6;
+__device__ __forceinline__ long long solve_flops(long long q0, long long p0, long long q, long long p) {
+    long long mm = p - p0;
+    long long f = 4 * mm * (p0 * q0 - p0 * (p0 - 1) / 2);
+    long long s2 = mm * (mm + 1) * (2 * mm + 1) / 6;
     f += (q - p) * (2 * mm + 2 * mm * (mm + 1)) + mm * (mm + 1) + 4 * s2;
-    return (double)(f + p * p);
+    return f + p * p;
 }
 
 template <class Team, typename T> struct Column {
@@ -107,8 +108,9 @@ template <class Team, typename T> struct Column {
     int64_t q0, p0;
     int rank_flag;
     double rho;
-    // per-column work counters (committed only when the column finishes)
-    double c_qr, c_res, c_ref, c_ref64, c_bytes, c_solves, c_drops, c_pmax, c_qmax;
+    // per-column work counters (integers; committed only when the column finishes)
+    long long c_qr, c_res, c_ref, c_ref64, c_bytes;
+    int c_solves, c_drops, c_pmax, c_qmax;
 
     __device__ Column(const Team &t, const DevA &a, const DevParams &pp, const Caps &c, Work<T> &ww, int32_t kk)
         : team(t), A(a), P(pp), cap(c), w(ww), k(kk) {}
@@ -127,7 +129,14 @@ template <class Team, typename T> struct Column {
             int tot;
             int off = team.scan(len, &tot);
             if (next_pow2(base + tot) > cap.scap) return false;
-            for (int e = 0; e < len; ++e) w.buf[base + off + e] = A.row_idx[st + e];
+            for (int e = 0; e < len; e += 4) {
+                int32_t v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = (e + u < len) ? A.row_idx[st + e + u] : 0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (e + u < len) w.buf[base + off + e + u] = v[u];
+            }
             base += tot;
         }
         team.sync();
@@ -157,13 +166,14 @@ template <class Team, typename T> struct Column {
             T v0 = x0 - alpha;
             T vtv = sigma - x0 * x0 + v0 * v0;
             if (vtv > T(0)) {
+                const T two_over = T(2) / vtv;
                 for (int c = j + 1; c <= p; ++c) {
                     T *t = (c < p) ? w.B + (int64_t)c * q : w.rhs;
                     T d = 0;
                     for (int i = me; i < q; i += Team::SIZE)
                         if (i >= j) d += ((i == j) ? v0 : col[i]) * t[i];
                     T sdot = team.sum(d);
-                    T f = T(2) * sdot / vtv;
+                    T f = sdot * two_over;
                     for (int i = me; i < q; i += Team::SIZE)
                         if (i >= j) t[i] -= f * ((i == j) ? v0 : col[i]);
                 }
@@ -173,11 +183,11 @@ template <class Team, typename T> struct Column {
                 col[j] = alpha;
                 w.vhead[j] = v0;
                 w.vtv[j] = vtv;
-                if (fabs((double)alpha) <= (double)small) rank_flag = 1;
+                if (fabs(alpha) <= small) rank_flag = 1;
             }
             team.sync();
         }
-        rank_flag = team.maxi(rank_flag);
+        rank_flag = team.maxv(rank_flag);
         back_substitute(small);
     }
 
@@ -186,7 +196,7 @@ template <class Team, typename T> struct Column {
         const int me = team.rank();
         for (int i = p - 1; i >= 0; --i) {
             T d = w.B[(int64_t)i * q + i];
-            T xi = (fabs((double)d) <= (double)small) ? T(0) : w.rhs[i] / d;
+            T xi = (fabs(d) <= small) ? T(0) : w.rhs[i] / d;
             team.sync();
             for (int c = me; c < i; c += Team::SIZE) w.rhs[c] -= w.B[(int64_t)i * q + c] * xi;
             if (me == 0) w.rhs[i] = xi;
@@ -205,7 +215,7 @@ template <class Team, typename T> struct Column {
                 for (int i = me; i < q; i += Team::SIZE)
                     if (i >= j) d += ((i == j) ? v0 : col[i]) * w.rhs[i];
                 T sdot = team.sum(d);
-                T f = T(2) * sdot / vtv;
+                T f = sdot * (T(2) / vtv);
                 for (int i = me; i < q; i += Team::SIZE)
                     if (i >= j) w.rhs[i] -= f * ((i == j) ? v0 : col[i]);
             }
@@ -229,22 +239,34 @@ template <class Team, typename T> struct Column {
             w.S[i] = row;
         }
         team.sync();
-        double ss = 0.0, cnt = 0.0;
+        double ss = 0.0;
+        int cnt = 0;
         for (int i = me; i < s; i += Team::SIZE) {
-            int32_t row = w.S[i];
+            const int32_t row = w.S[i];
+            const int64_t e0 = A.row_ptr[row], e1 = A.row_ptr[row + 1];
             double acc = 0.0;
-            for (int64_t e = A.row_ptr[row]; e < A.row_ptr[row + 1]; ++e) {
-                int pos = find_i32(w.J, p, A.col_idx[e]);
-                if (pos >= 0) { acc = fma(A.val[e], w.m[pos], acc); cnt += 1.0; }
+            for (int64_t e = e0; e < e1; e += 4) {
+                int32_t cj[4];
+                double av[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    cj[u] = (e + u < e1) ? A.col_idx[e + u] : -1;
+                    av[u] = (e + u < e1) ? A.val[e + u] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    int pos = (cj[u] >= 0) ? find_i32(w.J, p, cj[u]) : -1;
+                    if (pos >= 0) { acc = fma(av[u], w.m[pos], acc); ++cnt; }
+                }
             }
             if (row == k) acc -= 1.0;
             w.r[i] = acc;
-            ss += acc * acc;
+            ss = fma(acc, acc, ss);
         }
         rho = sqrt(team.sum(ss));
-        double nnzJ = team.sum(cnt);
-        if (refine) c_ref64 += 2.0 * nnzJ + 2.0 * (double)s;
-        else c_res += 2.0 * nnzJ + 2.0 * (double)s;
+        long long nnzJ = team.sum(cnt);
+        if (refine) c_ref64 += 2 * nnzJ + 2 * (long long)s;
+        else c_res += 2 * nnzJ + 2 * (long long)s;
         team.sync();
     }
 
@@ -259,19 +281,32 @@ template <class Team, typename T> struct Column {
         for (int64_t i = me; i < qp; i += Team::SIZE) w.B[i] = T(0);
         for (int i = me; i < q; i += Team::SIZE) w.rhs[i] = (w.I[i] == k) ? T(1) : T(0);
         team.sync();
-        double fro2 = 0.0;
+        T fro2 = 0;
         for (int c = me; c < p; c += Team::SIZE) {
-            int32_t j = w.J[c];
-            for (int64_t e = A.col_ptr[j]; e < A.col_ptr[j + 1]; ++e) {
-                int pos = find_i32(w.I, q, A.row_idx[e]);
-                double a = A.cval[e];
-                w.B[(int64_t)c * q + pos] = (T)a;
-                fro2 += a * a;
+            const int32_t j = w.J[c];
+            const int64_t e0 = A.col_ptr[j], e1 = A.col_ptr[j + 1];
+            T *Bc = w.B + (int64_t)c * q;
+            for (int64_t e = e0; e < e1; e += 4) {
+                int32_t ri[4];
+                double av[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    ri[u] = (e + u < e1) ? A.row_idx[e + u] : -1;
+                    av[u] = (e + u < e1) ? A.cval[e + u] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (ri[u] >= 0) {
+                        T a = (T)av[u];
+                        Bc[find_i32(w.I, q, ri[u])] = a;
+                        fro2 += a * a;
+                    }
+                }
             }
         }
-        double fro = sqrt(team.sum(fro2));
+        T fro = sqrt(team.sum(fro2));
         team.sync();
-        T small = (T)((double)q * Unit<T>::u * 2.0 * fro);
+        const T small = T(q) * T(2.0 * Unit<T>::u) * fro;
         rank_flag = 0;
         if (q < p) {  // more unknowns than rows: only possible for singular A
             for (int c = me; c < p; c += Team::SIZE) w.m[c] = 0.0;
@@ -294,39 +329,34 @@ template <class Team, typename T> struct Column {
                 apply_qt_solve(small);
                 for (int c = me; c < p; c += Team::SIZE) w.m[c] += (double)w.rhs[c];
                 team.sync();
-                c_ref += 4.0 * (double)q * (double)p + (double)p * (double)p;
+                c_ref += 4LL * q * p + (long long)p * p;
             }
         }
         c_qr += append ? solve_flops(q0, p0, q, p) : solve_flops(0, 0, q, p);
         q0 = q;
         p0 = p;
-        c_solves += 1.0;
-        c_pmax = fmax(c_pmax, (double)p);
-        c_qmax = fmax(c_qmax, (double)q);
+        c_solves += 1;
+        c_pmax = max(c_pmax, p);
+        c_qmax = max(c_qmax, q);
         return true;
     }
 
     // Eq. 4.3: drop |m_j| <= tau, keep at least the largest, re-solve once.
+    // Magnitudes are compared as ordered integer keys (exact).
     __device__ bool drop() {
         if (P.drop_mode == RSAI_DROP_NONE) return true;
         const int me = team.rank();
-        const double nrm1 = *P.norm1;
-        double tau = (P.drop_mode == RSAI_DROP_ADAPTIVE) ? P.eps / ((double)p * nrm1) : P.tol / nrm1;
+        const double tau = (P.drop_mode == RSAI_DROP_ADAPTIVE) ? P.eps / ((double)p * *P.norm1) : *P.tau_fixed;
+        const long long tk = abskey(tau);
         int nkeep = 0;
-        double ba = -1.0;
+        long long ba = -1;
         int bi = INT32_MAX;
         for (int c = me; c < p; c += Team::SIZE) {
-            double a = fabs(w.m[c]);
-            nkeep += (a > tau);
+            long long a = abskey(w.m[c]);
+            nkeep += (a > tk);
             if (dom_before(a, c, ba, bi)) { ba = a; bi = c; }
         }
-        int keep_total;
-        {
-            int tot = 0;
-            int part = nkeep;
-            tot = (int)team.sum((double)part);
-            keep_total = tot;
-        }
+        const int keep_total = team.sum(nkeep);
         if (keep_total == p) return true;
         if (keep_total == 0) {
             team.argmax(ba, bi);
@@ -340,7 +370,7 @@ template <class Team, typename T> struct Column {
             int base = 0;
             for (int c0 = 0; c0 < p; c0 += Team::SIZE) {
                 int c = c0 + me;
-                int f = (c < p) && (fabs(w.m[c]) > tau);
+                int f = (c < p) && (abskey(w.m[c]) > tk);
                 int tot;
                 int pos = team.scan(f, &tot);
                 if (f) w.Jn[base + pos] = w.J[c];
@@ -351,40 +381,40 @@ template <class Team, typename T> struct Column {
             p = base;
             team.sync();
         }
-        c_drops += 1.0;
+        c_drops += 1;
         return solve(false);
     }
 
     // Top-c dominant rows of S \ R (Algorithm 1 step 4) into w.Rhat; returns
-    // their number (0: no candidate left).
+    // their number (0: no candidate left).  |r_i| enters only as ordered
+    // integer keys; the tie band needs three double operations per call.
     __device__ int dominant_rows() {
         const int me = team.rank();
-        double rinf = 0.0;
-        for (int i = me; i < s; i += Team::SIZE) rinf = fmax(rinf, fabs(w.r[i]));
+        long long rinf = 0;
+        for (int i = me; i < s; i += Team::SIZE) rinf = max(rinf, abskey(w.r[i]));
         rinf = team.maxv(rinf);
-        const double band = P.tie_band * rinf;
+        const double band = P.tie_band * key_value(rinf);
+        const long long bk = abskey(band);
         int ncand = 0;
-        for (int i = me; i < s; i += Team::SIZE) {
-            double a = fabs(w.r[i]);
-            ncand += (a > band) && (find_i32(w.Rset, nR, w.S[i]) < 0);
-        }
-        ncand = (int)team.sum((double)ncand);
+        for (int i = me; i < s; i += Team::SIZE)
+            ncand += (abskey(w.r[i]) > bk) && (find_i32(w.Rset, nR, w.S[i]) < 0);
+        ncand = team.sum(ncand);
         if (ncand == 0) return 0;
         const int c = P.c;
-        bool take_all = ncand <= c;
-        double v = 0.0;
+        const bool take_all = ncand <= c;
+        long long hik = 0, lob = 0;
         if (!take_all) {
             // the c-th element of the (|r| desc, i asc) order: c rounds of argmax,
             // each over the candidates strictly after the previous pick
-            double pa = INFINITY;
+            long long pa = LLONG_MAX;
             int pi = -1;
             for (int t = 0; t < c; ++t) {
-                double ba = -1.0;
+                long long ba = -1;
                 int bi = INT32_MAX;
                 for (int i = me; i < s; i += Team::SIZE) {
-                    double a = fabs(w.r[i]);
+                    long long a = abskey(w.r[i]);
                     int32_t row = w.S[i];
-                    if (a > band && dom_before(pa, pi, a, row) && dom_before(a, row, ba, bi) &&
+                    if (a > bk && dom_before(pa, pi, a, row) && dom_before(a, row, ba, bi) &&
                         find_i32(w.Rset, nR, row) < 0) {
                         ba = a;
                         bi = row;
@@ -394,17 +424,19 @@ template <class Team, typename T> struct Column {
                 pa = ba;
                 pi = bi;
             }
-            v = pa;
+            const double v = key_value(pa);
+            hik = abskey(v + band);
+            lob = __double_as_longlong(v - band);  // negative bit pattern if v - band < 0
         }
-        // selection in index order: all candidates, or (above the band) +
-        // (lowest-index ties up to c)
+        // selection in index order: all candidates, or (above v + band) +
+        // (lowest-index entries within [v - band, v + band] up to c)
         int nabove = 0;
         if (!take_all) {
             for (int i = me; i < s; i += Team::SIZE) {
-                double a = fabs(w.r[i]);
-                nabove += (a > band) && (a - v > band) && (find_i32(w.Rset, nR, w.S[i]) < 0);
+                long long a = abskey(w.r[i]);
+                nabove += (a > bk) && (a > hik) && (find_i32(w.Rset, nR, w.S[i]) < 0);
             }
-            nabove = (int)team.sum((double)nabove);
+            nabove = team.sum(nabove);
         }
         const int need = c - nabove;
         int base = 0, tbase = 0;
@@ -412,11 +444,11 @@ template <class Team, typename T> struct Column {
             int i = i0 + me;
             int cand = 0, above = 0, tie = 0;
             if (i < s) {
-                double a = fabs(w.r[i]);
-                cand = (a > band) && (find_i32(w.Rset, nR, w.S[i]) < 0);
+                long long a = abskey(w.r[i]);
+                cand = (a > bk) && (find_i32(w.Rset, nR, w.S[i]) < 0);
                 if (cand && !take_all) {
-                    above = (a - v > band);
-                    tie = (fabs(a - v) <= band);
+                    above = a > hik;
+                    tie = (a >= lob) && (a <= hik);
                 }
             }
             int ttot;
@@ -460,7 +492,14 @@ template <class Team, typename T> struct Column {
         int tot;
         int off = team.scan(len, &tot);
         if (next_pow2(tot) > cap.scap) return -1;
-        for (int e = 0; e < len; ++e) w.buf[off + e] = A.col_idx[st + e];
+        for (int e = 0; e < len; e += 4) {
+            int32_t v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = (e + u < len) ? A.col_idx[st + e + u] : 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (e + u < len) w.buf[off + e + u] = v[u];
+        }
         team.sync();
         team_sort_i32(team, w.buf, tot);
         int nu = team_unique_i32(team, w.buf, tot, w.buf2);
@@ -492,10 +531,10 @@ template <class Team, typename T> struct Column {
 
     // algorithmic bytes of columns entering J: 12 per nonzero + 16 of pointers
     __device__ void note_bytes_columns(int from, int count, const int32_t *list) {
-        double b = 0.0;
+        long long b = 0;
         for (int t = from + team.rank(); t < from + count; t += Team::SIZE) {
             int32_t j = list[t];
-            b += 12.0 * (double)(A.col_ptr[j + 1] - A.col_ptr[j]) + 16.0;
+            b += 12 * (A.col_ptr[j + 1] - A.col_ptr[j]) + 16;
         }
         c_bytes += team.sum(b);
     }
@@ -504,11 +543,11 @@ template <class Team, typename T> struct Column {
     __device__ int run() {
         const int me = team.rank();
         p = 1; q = 0; s = 0; nR = 0; l = 0; q0 = 0; p0 = 0; rank_flag = 0; rho = 0.0;
-        c_qr = c_res = c_ref = c_ref64 = c_bytes = c_solves = c_drops = 0.0;
-        c_pmax = c_qmax = 0.0;
+        c_qr = c_res = c_ref = c_ref64 = c_bytes = 0;
+        c_solves = c_drops = c_pmax = c_qmax = 0;
         if (me == 0) w.J[0] = k;
         team.sync();
-        c_bytes += 12.0 * (double)(A.col_ptr[k + 1] - A.col_ptr[k]) + 16.0;
+        c_bytes += 12 * (A.col_ptr[k + 1] - A.col_ptr[k]) + 16;
         if (!solve(false)) return COL_OVERFLOW;
         if (!drop()) return COL_OVERFLOW;
         residual();
@@ -517,8 +556,8 @@ template <class Team, typename T> struct Column {
             if (nh == 0) break;
             if (!add_to_R(nh)) return COL_OVERFLOW;
             {
-                double b = 0.0;
-                if (me < nh) b = 4.0 * (double)(A.row_ptr[w.Rhat[me] + 1] - A.row_ptr[w.Rhat[me]]) + 16.0;
+                long long b = 0;
+                if (me < nh) b = 4 * (A.row_ptr[w.Rhat[me] + 1] - A.row_ptr[w.Rhat[me]]) + 16;
                 c_bytes += team.sum(b);
             }
             int nj = new_columns(nh);
@@ -531,7 +570,7 @@ template <class Team, typename T> struct Column {
             if (!drop()) return COL_OVERFLOW;
             residual();
         }
-        c_bytes += 36.0 * (double)p;
+        c_bytes += 36LL * p;
         return COL_DONE;
     }
 };

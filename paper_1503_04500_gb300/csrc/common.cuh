@@ -9,6 +9,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <climits>
 
 #include "../../include/rsai.h"
 
@@ -30,7 +31,8 @@ struct DevA {
 struct DevParams {
     int c, l_max, drop_mode, precision;
     double eps, tol, tie_band;
-    const double *norm1;  // ||A||_1 on the device (computed by a kernel)
+    const double *norm1;      // ||A||_1 on the device (computed by a kernel)
+    const double *tau_fixed;  // tol / ||A||_1 (computed once per build)
 };
 
 // Work counters of one team, summed into the global statistics at the end.
@@ -84,8 +86,18 @@ __device__ __forceinline__ int find_i32(const int32_t *a, int len, int32_t v) {
     return (p < len && a[p] == v) ? p : -1;
 }
 
+// |x| of a double as an ordered integer key: for x >= 0 the IEEE bit pattern
+// orders like the value, so comparisons of magnitudes need no FP64 pipe.
+__device__ __forceinline__ long long abskey(double x) {
+    return __double_as_longlong(x) & 0x7fffffffffffffffLL;
+}
+__device__ __forceinline__ double key_value(long long k) { return __longlong_as_double(k); }
+__device__ __forceinline__ bool finite_bits(double x) {
+    return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+
 // (a, i) ordered by a descending, then i ascending: true if (a,i) comes first.
-__device__ __forceinline__ bool dom_before(double a, int i, double b, int j) {
+__device__ __forceinline__ bool dom_before(long long a, int i, long long b, int j) {
     return a > b || (a == b && i < j);
 }
 
@@ -99,21 +111,19 @@ struct WarpTeam {
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         return x;
     }
-    __device__ __forceinline__ double maxv(double x) const {
+    template <typename V> __device__ __forceinline__ V maxv(V x) const {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
-        return x;
-    }
-    __device__ __forceinline__ int maxi(int x) const {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
+        for (int o = 16; o > 0; o >>= 1) {
+            V y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = y > x ? y : x;
+        }
         return x;
     }
     // argmax under dom_before; returns the winner to every lane
-    __device__ __forceinline__ void argmax(double &a, int &i) const {
+    __device__ __forceinline__ void argmax(long long &a, int &i) const {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            double b = __shfl_xor_sync(0xffffffffu, a, o);
+            long long b = __shfl_xor_sync(0xffffffffu, a, o);
             int j = __shfl_xor_sync(0xffffffffu, i, o);
             if (dom_before(b, j, a, i)) { a = b; i = j; }
         }
@@ -135,62 +145,56 @@ struct WarpTeam {
     }
 };
 
-// A whole CTA of NT threads; `red` is NT/32+1 doubles and ints of shared scratch.
+// A whole CTA of NT threads; `red` is NT/32+1 words of shared scratch (8 bytes
+// each, holding any reduced type), `redi` as many ints.
 template <int NT> struct BlockTeam {
     static constexpr int SIZE = NT;
     static constexpr int NW = NT / 32;
-    double *redd;
+    unsigned long long *red;
     int *redi;
     __device__ __forceinline__ int rank() const { return threadIdx.x; }
     __device__ __forceinline__ void sync() const { __syncthreads(); }
+    template <typename V> __device__ __forceinline__ V &slot(int w) const { return *reinterpret_cast<V *>(&red[w]); }
     template <typename V> __device__ __forceinline__ V sum(V x) const {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         __syncthreads();
-        if ((threadIdx.x & 31) == 0) redd[threadIdx.x >> 5] = (double)x;
+        if ((threadIdx.x & 31) == 0) slot<V>(threadIdx.x >> 5) = x;
         __syncthreads();
-        V s = 0;
+        V s = slot<V>(0);
 #pragma unroll
-        for (int w = 0; w < NW; ++w) s += (V)redd[w];
+        for (int w = 1; w < NW; ++w) s += slot<V>(w);
         return s;
     }
-    __device__ __forceinline__ double maxv(double x) const {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) redd[threadIdx.x >> 5] = x;
-        __syncthreads();
-        double s = redd[0];
-#pragma unroll
-        for (int w = 1; w < NW; ++w) s = fmax(s, redd[w]);
-        return s;
-    }
-    __device__ __forceinline__ int maxi(int x) const {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) redi[threadIdx.x >> 5] = x;
-        __syncthreads();
-        int s = redi[0];
-#pragma unroll
-        for (int w = 1; w < NW; ++w) s = max(s, redi[w]);
-        return s;
-    }
-    __device__ __forceinline__ void argmax(double &a, int &i) const {
+    template <typename V> __device__ __forceinline__ V maxv(V x) const {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            double b = __shfl_xor_sync(0xffffffffu, a, o);
+            V y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = y > x ? y : x;
+        }
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) slot<V>(threadIdx.x >> 5) = x;
+        __syncthreads();
+        V s = slot<V>(0);
+#pragma unroll
+        for (int w = 1; w < NW; ++w) s = slot<V>(w) > s ? slot<V>(w) : s;
+        return s;
+    }
+    __device__ __forceinline__ void argmax(long long &a, int &i) const {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            long long b = __shfl_xor_sync(0xffffffffu, a, o);
             int j = __shfl_xor_sync(0xffffffffu, i, o);
             if (dom_before(b, j, a, i)) { a = b; i = j; }
         }
         __syncthreads();
-        if ((threadIdx.x & 31) == 0) { redd[threadIdx.x >> 5] = a; redi[threadIdx.x >> 5] = i; }
+        if ((threadIdx.x & 31) == 0) { slot<long long>(threadIdx.x >> 5) = a; redi[threadIdx.x >> 5] = i; }
         __syncthreads();
-        a = redd[0];
+        a = slot<long long>(0);
         i = redi[0];
 #pragma unroll
         for (int w = 1; w < NW; ++w)
-            if (dom_before(redd[w], redi[w], a, i)) { a = redd[w]; i = redi[w]; }
+            if (dom_before(slot<long long>(w), redi[w], a, i)) { a = slot<long long>(w); i = redi[w]; }
     }
     __device__ __forceinline__ int scan(int x, int *total) const {
         int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -215,9 +219,9 @@ template <int NT> struct BlockTeam {
     }
     template <typename V> __device__ __forceinline__ V bcast(V x, int src) const {
         __syncthreads();
-        if ((int)threadIdx.x == src) redd[NW] = (double)x;
+        if ((int)threadIdx.x == src) slot<V>(NW) = x;
         __syncthreads();
-        return (V)redd[NW];
+        return slot<V>(NW);
     }
 };
 

@@ -7,6 +7,7 @@ namespace rsai {
 
 constexpr int kBlockThreads = 256;  // CTA team size of bins C and G
 constexpr int kWarpsPerCta = 4;     // warps per CTA in bin W
+constexpr int kStatBlocks = 256;    // blocks of the per-column statistics reduction
 
 // input checks, ||A||_1, statistics, scan, assembly
 __global__ void k_check_ptr(const int64_t *ptr, int64_t n, int64_t nnz, int32_t *err);
@@ -15,7 +16,9 @@ __global__ void k_csc_map(DevA A, int64_t *csc_to_csr, int32_t *err);
 __global__ void k_csc_from_csr(const double *csr_val, const int64_t *csc_to_csr, double *cval, int64_t nnz);
 __global__ void k_norm1(const int64_t *col_ptr, const double *cval, int64_t n, double *out);
 __global__ void k_column_stats(const double *rho, const int32_t *flags, const int32_t *len, int64_t n, double eps,
-                               double *out);
+                               double *partial, unsigned long long *counts);
+__global__ void k_column_stats_final(const double *partial, double *frob2);
+__global__ void k_tau_fixed(const double *norm1, double tol, double *tau);
 __global__ void k_scan_blocks(const int32_t *in, int64_t n, int64_t *out, int64_t *block_sums);
 __global__ void k_scan_sums(int64_t *block_sums, int64_t nb, int64_t *total);
 __global__ void k_scan_add(int64_t *out, int64_t n, const int64_t *block_sums, const int64_t *total);
@@ -31,9 +34,10 @@ __global__ void k_sort_rows(const int64_t *Mrowptr, const int32_t *tcols, const 
 template <typename T> size_t work_bytes(const Caps &c);
 
 cudaError_t launch_bin_warp(bool fp32, int grid, int warps, const DevA &A, const DevParams &P, const Caps &cap,
-                            const ColQueue &Q, const ColOut &O, double *gctr, bool last, cudaStream_t st);
+                            const ColQueue &Q, const ColOut &O, unsigned long long *gctr, bool last,
+                            cudaStream_t st);
 cudaError_t launch_bin_block(bool fp32, int grid, const DevA &A, const DevParams &P, const Caps &cap,
-                             const ColQueue &Q, const ColOut &O, double *gctr, bool last, char *gwork,
+                             const ColQueue &Q, const ColOut &O, unsigned long long *gctr, bool last, char *gwork,
                              size_t gstride, int bin, cudaStream_t st);
 int occupancy_bin_warp(bool fp32, int warps, const Caps &cap);
 int occupancy_bin_block(bool fp32, const Caps &cap, bool global_work);

@@ -26,8 +26,8 @@ struct rsai_handle {
     int64_t *row_ptr = nullptr, *col_ptr = nullptr, *csc_to_csr = nullptr;
     int32_t *col_idx = nullptr, *row_idx = nullptr;
     double *val = nullptr, *cval = nullptr;
-    // scalars / counters: [0] norm1, [1..] gctr (CTR_COUNT + 3), then column stats (3)
-    double *dscal = nullptr;
+    // 8-byte words: norm1, tau_fixed, frob2, counters, column counts, partial sums
+    unsigned long long *dscal = nullptr;
     int32_t *err = nullptr;
     uint32_t *qnext = nullptr;   // [3] queue counters, [3..4] overflow counts
     int32_t *ovf1 = nullptr, *ovf2 = nullptr;
@@ -64,8 +64,13 @@ struct rsai_handle {
 
 namespace {
 
-constexpr int kScalars = 1 + CTR_COUNT + 3 + 3;
-constexpr int kStatsAt = 1 + CTR_COUNT + 3;
+// layout of the scalar block (8-byte words)
+constexpr int kNorm1 = 0, kTau = 1, kFrob2 = 2, kCtr = 3;
+constexpr int kCounts = kCtr + CTR_COUNT + 3;
+constexpr int kPartial = kCounts + 2;
+constexpr int kScalars = kPartial + kStatBlocks;
+
+double *dword(const rsai_handle *h, int at) { return reinterpret_cast<double *>(h->dscal + at); }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? RSAI_OK : RSAI_ERR_CUDA; }
 
@@ -99,7 +104,8 @@ DevParams dev_params(const rsai_handle *h) {
     P.eps = h->params.eps;
     P.tol = h->params.tol;
     P.tie_band = h->params.tie_band;
-    P.norm1 = h->dscal;
+    P.norm1 = dword(h, kNorm1);
+    P.tau_fixed = dword(h, kTau);
     return P;
 }
 
@@ -119,18 +125,19 @@ cudaError_t scan_counts(rsai_handle *h, const int32_t *in, int64_t *out, cudaStr
 cudaError_t enqueue_build(rsai_handle *h, cudaStream_t st, cudaEvent_t *ev = nullptr) {
     const int64_t n = h->n;
     if (ev) cudaEventRecord(ev[0], st);
-    cudaMemsetAsync(h->dscal, 0, sizeof(double) * kScalars, st);
+    cudaMemsetAsync(h->dscal, 0, sizeof(unsigned long long) * kScalars, st);
     cudaMemsetAsync(h->err, 0, sizeof(int32_t), st);
     cudaMemsetAsync(h->qnext, 0, sizeof(uint32_t) * 8, st);
     cudaMemsetAsync(h->pool_top, 0, sizeof(unsigned long long), st);
     cudaMemsetAsync(h->row_count, 0, sizeof(int32_t) * (size_t)n, st);
     cudaMemsetAsync(h->cursor, 0, sizeof(int32_t) * (size_t)n, st);
-    k_norm1<<<blocks(n, 256), 256, 0, st>>>(h->col_ptr, h->cval, n, h->dscal);
+    k_norm1<<<blocks(n, 256), 256, 0, st>>>(h->col_ptr, h->cval, n, dword(h, kNorm1));
+    k_tau_fixed<<<1, 1, 0, st>>>(dword(h, kNorm1), h->params.tol, dword(h, kTau));
 
     const DevA A = dev_a(h);
     const DevParams P = dev_params(h);
     const bool fp32 = h->params.precision == RSAI_FP32_REFINE;
-    double *gctr = h->dscal + 1;
+    unsigned long long *gctr = h->dscal + kCtr;
     ColOut O{h->col_off, h->col_len, h->rho, h->loops, h->flags, h->pool_rows, h->pool_vals,
              h->pool_cap, h->pool_top, h->err};
     ColQueue QW{nullptr, nullptr, n, h->qnext + 0, h->ovf1, h->qnext + 3, h->ovf_cap};
@@ -146,7 +153,9 @@ cudaError_t enqueue_build(rsai_handle *h, cudaStream_t st, cudaEvent_t *ev = nul
     e = launch_bin_block(fp32, h->grid_g, A, P, h->capG, QG, O, gctr, true, h->gwork, h->gstride, 2, st);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[4], st);
-    k_column_stats<<<1, 1024, 0, st>>>(h->rho, h->flags, h->col_len, n, h->params.eps, h->dscal + kStatsAt);
+    k_column_stats<<<kStatBlocks, 256, 0, st>>>(h->rho, h->flags, h->col_len, n, h->params.eps,
+                                                dword(h, kPartial), h->dscal + kCounts);
+    k_column_stats_final<<<1, kStatBlocks, 0, st>>>(dword(h, kPartial), dword(h, kFrob2));
     // M in CSC, then CSR with rows sorted by column index
     e = scan_counts(h, h->col_len, h->Mcolptr, st);
     if (e != cudaSuccess) return e;
@@ -381,10 +390,10 @@ rsai_status rsai_build(const rsai_csr *A, const rsai_csc *Acsc, const rsai_param
     }
     {
         // many columns in the global bin: give it one CTA per SM for later rebuilds
-        double cnt = 0.0;
-        cudaMemcpyAsync(&cnt, h->dscal + 1 + CTR_COUNT + 2, sizeof(double), cudaMemcpyDeviceToHost, st);
+        unsigned long long cnt = 0;
+        cudaMemcpyAsync(&cnt, h->dscal + kCtr + CTR_COUNT + 2, sizeof(cnt), cudaMemcpyDeviceToHost, st);
         TRY(cuda_status(cudaStreamSynchronize(st)));
-        if (cnt > 16.0 * h->grid_g && h->grid_g < h->sms) {
+        if (cnt > 16ull * (unsigned long long)h->grid_g && h->grid_g < h->sms) {
             cudaFreeAsync(h->gwork, st);
             h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void *)h->gwork), h->allocs.end());
             h->grid_g = h->sms;
@@ -434,21 +443,26 @@ rsai_status rsai_rebuild(rsai_handle *h, void *stream) {
 rsai_status rsai_get_stats(rsai_handle *h, void *stream, rsai_stats *out) {
     if (!h || !out) return RSAI_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    double s[kScalars];
+    unsigned long long s[kCounts + 2];
     int32_t herr = 0;
     if (cudaMemcpyAsync(s, h->dscal, sizeof(s), cudaMemcpyDeviceToHost, st) != cudaSuccess) return RSAI_ERR_CUDA;
     cudaMemcpyAsync(&herr, h->err, sizeof(herr), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return RSAI_ERR_CUDA;
-    const double *c = s + 1;
+    auto dbl = [&](int at) {
+        double v;
+        memcpy(&v, &s[at], sizeof(v));
+        return v;
+    };
+    const unsigned long long *c = s + kCtr;
     memset(out, 0, sizeof(*out));
     out->n = h->n;
     out->nnz_A = h->nnz;
-    out->norm1_A = s[0];
-    out->qr_flops = c[CTR_QR];
-    out->res_flops = c[CTR_RES];
-    out->refine_flops = c[CTR_REFINE];
-    out->refine_flops_f64 = c[CTR_REFINE64];
-    out->bytes = c[CTR_BYTES];
+    out->norm1_A = dbl(kNorm1);
+    out->qr_flops = (double)c[CTR_QR];
+    out->res_flops = (double)c[CTR_RES];
+    out->refine_flops = (double)c[CTR_REFINE];
+    out->refine_flops_f64 = (double)c[CTR_REFINE64];
+    out->bytes = (double)c[CTR_BYTES];
     out->loops = (int64_t)c[CTR_LOOPS];
     out->solves = (int64_t)c[CTR_SOLVES];
     out->drops = (int64_t)c[CTR_DROPS];
@@ -458,9 +472,9 @@ rsai_status rsai_get_stats(rsai_handle *h, void *stream, rsai_stats *out) {
     out->n_nonfinite = (int64_t)c[CTR_NONFINITE];
     out->n_failed = (int64_t)c[CTR_FAILED];
     for (int b = 0; b < 3; ++b) out->cols_bin[b] = (int64_t)c[CTR_COUNT + b];
-    out->frob = std::sqrt(s[kStatsAt + 0]);
-    out->n_c = (int64_t)s[kStatsAt + 1];
-    out->nnz_M = (int64_t)s[kStatsAt + 2];
+    out->frob = std::sqrt(dbl(kFrob2));
+    out->n_c = (int64_t)s[kCounts + 0];
+    out->nnz_M = (int64_t)s[kCounts + 1];
     return herr ? (rsai_status)herr : RSAI_OK;
 }
 
