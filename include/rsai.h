@@ -52,7 +52,8 @@ typedef enum {
     RSAI_ERR_WORKSPACE = 9,     /* a column outgrew every size bin (see rsai_stats) */
     RSAI_ERR_BREAKDOWN = 10,    /* BiCGStab breakdown (rho = 0 or omega = 0) */
     RSAI_ERR_NOT_CONVERGED = 11,/* BiCGStab reached maxit */
-    RSAI_ERR_NO_DEVICE = 12     /* no CUDA device is visible */
+    RSAI_ERR_NO_DEVICE = 12,    /* no CUDA device is visible */
+    RSAI_ERR_TOO_LARGE = 13     /* problem larger than a fixed-size workspace */
 } rsai_status;
 
 /* Sparse A in CSR (row_ptr[n+1], col_idx[nnz], val[nnz]). */
@@ -246,6 +247,25 @@ enum {
  * the same as rsai_rebuild's.
  */
 rsai_status rsai_build_phase_times(rsai_handle *h, void *stream, double *ms);
+
+/*
+ * rsai_bicgstab_noalloc -- the solve of rsai_bicgstab for callers that must not
+ * allocate device memory (for example code running inside another
+ * framework's memory pool or plugin interface, or a real-time loop where an
+ * allocation and its implicit synchronisation are not allowed).  The paper has
+ * no counterpart: this is a deployment variant of rsai_bicgstab.
+ *   A : device CSR of A;  M : device CSR of the preconditioner (e.g. copied out
+ *       with rsai_get_M) or NULL;  b, x : device arrays of length n.
+ * It allocates nothing: its work vectors live in one fixed device array inside
+ * the library (about 4.7 MB, held by every GPU that loads the library until the
+ * process exits) and n must not exceed 65536 (else RSAI_ERR_TOO_LARGE).  The
+ * array's device address is looked up on the first call on each device, so
+ * make that first call before any stream capture.  Every call shares the
+ * array: calls that overlap on the GPU race and must be ordered on one stream.
+ * Same results, statuses and outputs as rsai_bicgstab.
+ */
+rsai_status rsai_bicgstab_noalloc(const rsai_csr *A, const rsai_csr *M, const double *b, double *x, double rtol,
+                                  int32_t maxit, int32_t *iters, double *relres, void *stream);
 
 /* Release a handle and its device memory (NULL is a no-op). */
 void rsai_handle_free(rsai_handle *h);

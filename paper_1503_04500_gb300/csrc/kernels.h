@@ -50,6 +50,19 @@ int bicgstab_run(int64_t n, const int64_t *Arp, const int32_t *Aci, const double
                  const int32_t *Mci, const double *Mv, const double *b, double *x, double rtol, int maxit,
                  int *iters, double *relres, cudaStream_t st);
 
+// BiCGStab vector steps (apply_kernels.cu); scalars on the device
+__global__ void k_bicg_p(int64_t n, const double *sc, const double *r, const double *v, double *p);
+__global__ void k_bicg_alpha(double *sc);
+__global__ void k_bicg_s(int64_t n, const double *sc, const double *r, const double *v, double *s);
+__global__ void k_bicg_half(int64_t n, const double *sc, const double *p, double *y);
+__global__ void k_bicg_omega(double *sc);
+__global__ void k_bicg_update(int64_t n, const double *sc, const double *p, const double *s, const double *t,
+                              double *y, double *r);
+__global__ void k_bicg_shift(double *sc);
+__global__ void k_bicg_init(int64_t n, const double *b, double *r, double *rhat, double *p, double *v, double *y,
+                            double *sc);
+__global__ void k_axpy_sub(int64_t n, const double *b, const double *ax, double *out);
+
 // FMA-chain peak (peak_kernels.cu)
 cudaError_t run_peak_fma(bool fp64, cudaStream_t st, double *flops_per_s);
 

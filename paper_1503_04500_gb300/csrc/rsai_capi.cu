@@ -235,6 +235,7 @@ const char *rsai_status_string(rsai_status s) {
         case RSAI_ERR_BREAKDOWN: return "BiCGStab breakdown";
         case RSAI_ERR_NOT_CONVERGED: return "BiCGStab did not converge within maxit";
         case RSAI_ERR_NO_DEVICE: return "no CUDA device";
+        case RSAI_ERR_TOO_LARGE: return "problem larger than the fixed-size workspace of this entry point";
     }
     return "unknown status";
 }

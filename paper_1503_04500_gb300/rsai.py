@@ -20,6 +20,7 @@ RSAI_OK = 0
 STATUS_NAMES = {
     0: "OK", 1: "INVALID_ARG", 2: "SHAPE", 3: "UNSORTED", 4: "INDEX_RANGE", 5: "EMPTY_COLUMN", 6: "OOM",
     7: "CUDA", 8: "TIMEOUT", 9: "WORKSPACE", 10: "BREAKDOWN", 11: "NOT_CONVERGED", 12: "NO_DEVICE",
+    13: "TOO_LARGE",
 }
 DROP = {"none": 0, "adaptive": 1, "fixed": 2}
 PRECISION = {"fp64": 0, "fp32_refine": 1}
@@ -31,6 +32,7 @@ EXPORTS = [
     "rsai_abi_version", "rsai_status_string", "rsai_params_default", "rsai_params_check", "rsai_build",
     "rsai_rebuild", "rsai_set_values", "rsai_get_stats", "rsai_get_M", "rsai_get_columns", "rsai_refit",
     "rsai_apply", "rsai_backward", "rsai_bicgstab", "rsai_handle_free", "rsai_peak_fma", "rsai_build_phase_times",
+    "rsai_bicgstab_noalloc",
 ]
 
 
@@ -111,6 +113,8 @@ def load(build_if_missing: bool = False):
         "rsai_handle_free": (None, [vp]),
         "rsai_peak_fma": (i32, [i32, vp, ctypes.POINTER(f64)]),
         "rsai_build_phase_times": (i32, [vp, vp, ctypes.POINTER(f64)]),
+        "rsai_bicgstab_noalloc": (i32, [ctypes.POINTER(CSR), ctypes.POINTER(CSR), vp, vp, f64, i32,
+                                        ctypes.POINTER(i32), ctypes.POINTER(f64), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -326,6 +330,26 @@ def bicgstab(A: DeviceMatrix, M: Handle | None, b, rtol=1e-8, maxit=1000, stream
                               int(maxit), ctypes.byref(it), ctypes.byref(rr), _stream(stream))
     _check(st, "rsai_bicgstab", ok=(RSAI_OK, 10, 11))
     return x, it.value, rr.value, st
+
+
+def bicgstab_noalloc(A: DeviceMatrix, M_csr, b, x, rtol=1e-8, maxit=1000, stream=None):
+    """rsai_bicgstab_noalloc: the same solve with no device allocation (n <= 65536).
+
+    ``M_csr`` is (row_ptr, col_idx, val) device tensors or None; ``x`` is a
+    caller-owned device output.  Returns (iters, relres, status).
+    """
+    it = ctypes.c_int32(0)
+    rr = ctypes.c_double(0.0)
+    csr = A.csr()
+    mcsr = None
+    if M_csr is not None:
+        rp, ci, va = M_csr
+        mcsr = CSR(A.n, int(va.numel()), _ptr(rp), _ptr(ci), _ptr(va))
+    st = load().rsai_bicgstab_noalloc(ctypes.byref(csr), None if mcsr is None else ctypes.byref(mcsr), _ptr(b),
+                                      _ptr(x), float(rtol), int(maxit), ctypes.byref(it), ctypes.byref(rr),
+                                      _stream(stream))
+    _check(st, "rsai_bicgstab_noalloc", ok=(RSAI_OK, 10, 11))
+    return it.value, rr.value, st
 
 
 def peak_fma(fp64: bool, stream=None) -> float:

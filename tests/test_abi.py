@@ -33,7 +33,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_abi_version_and_status_strings(lib):
     assert lib.rsai_abi_version() == 1
-    for code in range(0, 13):
+    for code in range(0, 14):
         s = rsai.status_string(code)
         assert s and s != "unknown status"
     assert rsai.status_string(999) == "unknown status"
