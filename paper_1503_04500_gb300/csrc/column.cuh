@@ -22,7 +22,10 @@
 // caller hands it to the next (larger) bin, which restarts it from J = {k}.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
+#include "warp_small.cuh"
 
 namespace rsai {
 
@@ -78,6 +81,19 @@ template <typename T> struct Work {
 };
 
 enum ColStatus { COL_DONE = 0, COL_OVERFLOW = 1 };
+
+// Sort buf[0..len) ascending: registers and shuffles on a warp (up to 256
+// elements), bitonic in shared memory otherwise.
+template <class Team>
+__device__ void team_sort_i32(const Team &team, int32_t *buf, int len) {
+    if constexpr (std::is_same<Team, WarpTeam>::value) {
+        if (len <= 32) { warp_sort_regs<1>(buf, len); return; }
+        if (len <= 64) { warp_sort_regs<2>(buf, len); return; }
+        if (len <= 128) { warp_sort_regs<4>(buf, len); return; }
+        if (len <= 256) { warp_sort_regs<8>(buf, len); return; }
+    }
+    team_sort_i32_smem(team, buf, len);
+}
 
 __host__ __device__ inline int next_pow2(int x) {
     int n = 1;
@@ -153,6 +169,12 @@ template <class Team, typename T> struct Column {
     // into rhs[0..p).  Keeps the reflectors (v_j below the diagonal of B,
     // heads in vhead, v^T v in vtv) for the refinement solve.
     __device__ void qr_solve(T small) {
+        if constexpr (std::is_same<Team, WarpTeam>::value) {
+            if (p <= kSmallP && q <= kSmallQ) {
+                rank_flag = warp_qr_small(w.B, q, p, w.rhs, w.vhead, w.vtv, small);
+                return;
+            }
+        }
         const int me = team.rank();
         for (int j = 0; j < p; ++j) {
             T *col = w.B + (int64_t)j * q;
@@ -206,6 +228,12 @@ template <class Team, typename T> struct Column {
 
     // rhs <- Q^T rhs with the stored reflectors, then R^{-1}
     __device__ void apply_qt_solve(T small) {
+        if constexpr (std::is_same<Team, WarpTeam>::value) {
+            if (p <= kSmallP && q <= kSmallQ) {
+                warp_apply_qt_small(w.B, q, p, w.rhs, w.vhead, w.vtv, small);
+                return;
+            }
+        }
         const int me = team.rank();
         for (int j = 0; j < p; ++j) {
             const T *col = w.B + (int64_t)j * q;

@@ -1,0 +1,195 @@
+// warp_small.cuh -- register-resident Householder QR for small LS problems on
+// one warp (|J| = p <= 16, |I| = q <= 64), the common case of stencil
+// matrices.
+//
+// Lane l holds rows l and l+32 of B (two registers per column); the loops over
+// the Householder step j and the trailing columns c are unrolled so that every
+// register index is a compile-time constant.  The (p - j) dot products of a
+// step are independent warp reductions that the compiler interleaves.  B is
+// read from and written back to the team workspace (column-major, ld = q),
+// leaving R above the diagonal and the reflector tails below it, exactly as the
+// shared-memory version does, so the solves that follow are unchanged.
+#pragma once
+
+#include "common.cuh"
+
+namespace rsai {
+
+constexpr int kSmallP = 16;
+constexpr int kSmallQ = 64;
+
+template <typename T> __device__ __forceinline__ T warp_sum_t(T x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Householder QR of B (q x p, ld q) applied to rhs, then back substitution into
+// rhs[0..p).  vhead/vtv receive v_j(j) and v_j^T v_j.  Returns the rank flag.
+template <typename T>
+__device__ int warp_qr_small(T *B, int q, int p, T *rhs, T *vhead, T *vtv, T small) {
+    const int lane = threadIdx.x & 31;
+    const bool h0 = lane < q, h1 = lane + 32 < q;
+    T b0[kSmallP], b1[kSmallP];
+#pragma unroll
+    for (int c = 0; c < kSmallP; ++c) {
+        b0[c] = (c < p && h0) ? B[c * q + lane] : T(0);
+        b1[c] = (c < p && h1) ? B[c * q + lane + 32] : T(0);
+    }
+    T r0 = h0 ? rhs[lane] : T(0);
+    T r1 = h1 ? rhs[lane + 32] : T(0);
+    int rank = 0;
+#pragma unroll
+    for (int j = 0; j < kSmallP; ++j) {
+        if (j < p) {
+            // reflector of column j over rows >= j (rows >= q hold zeros)
+            T v0 = (lane >= j) ? b0[j] : T(0);
+            T v1 = b1[j];
+            const T sigma = warp_sum_t(v0 * v0 + v1 * v1);
+            const T x0 = __shfl_sync(0xffffffffu, b0[j], j);
+            const T nrm = sqrt(sigma);
+            const T alpha = (x0 >= T(0)) ? -nrm : nrm;
+            const T vh = x0 - alpha;
+            const T vv = sigma - x0 * x0 + vh * vh;
+            if (lane == j) v0 = vh;
+            if (vv > T(0)) {
+                const T two_over = T(2) / vv;
+                T d[kSmallP + 1];
+#pragma unroll
+                for (int c = j + 1; c < kSmallP; ++c) d[c] = (c < p) ? v0 * b0[c] + v1 * b1[c] : T(0);
+                d[kSmallP] = v0 * r0 + v1 * r1;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                    for (int c = j + 1; c <= kSmallP; ++c)
+                        if (c == kSmallP || c < p) d[c] += __shfl_xor_sync(0xffffffffu, d[c], o);
+                }
+#pragma unroll
+                for (int c = j + 1; c < kSmallP; ++c) {
+                    if (c < p) {
+                        const T f = d[c] * two_over;
+                        b0[c] -= f * v0;
+                        b1[c] -= f * v1;
+                    }
+                }
+                const T fr = d[kSmallP] * two_over;
+                r0 -= fr * v0;
+                r1 -= fr * v1;
+            }
+            if (lane == j) b0[j] = alpha;  // R_jj; rows > j keep the reflector tail
+            if (lane == 0) {
+                vhead[j] = vh;
+                vtv[j] = vv;
+            }
+            rank |= (fabs(alpha) <= small) ? 1 : 0;
+        }
+    }
+    // back substitution on R (row i of R lives in lane i, slot b0)
+    T x = T(0);
+#pragma unroll
+    for (int i = kSmallP - 1; i >= 0; --i) {
+        if (i < p) {
+            const T di = __shfl_sync(0xffffffffu, b0[i], i);
+            const T yi = __shfl_sync(0xffffffffu, r0, i);
+            const T xi = (fabs(di) <= small) ? T(0) : yi / di;
+            if (lane == i) x = xi;
+            if (lane < i) r0 -= b0[i] * xi;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < kSmallP; ++c) {
+        if (c < p) {
+            if (h0) B[c * q + lane] = b0[c];
+            if (h1) B[c * q + lane + 32] = b1[c];
+        }
+    }
+    if (lane < p) rhs[lane] = x;
+    __syncwarp();
+    return rank;
+}
+
+// rhs <- R^{-1} Q^T rhs with the reflectors left in B by warp_qr_small
+template <typename T>
+__device__ void warp_apply_qt_small(const T *B, int q, int p, T *rhs, const T *vhead, const T *vtv, T small) {
+    const int lane = threadIdx.x & 31;
+    const bool h0 = lane < q, h1 = lane + 32 < q;
+    T r0 = h0 ? rhs[lane] : T(0);
+    T r1 = h1 ? rhs[lane + 32] : T(0);
+    T rrow[kSmallP];  // row `lane` of R (for the back substitution)
+#pragma unroll
+    for (int j = 0; j < kSmallP; ++j) {
+        rrow[j] = (j < p && h0) ? B[j * q + lane] : T(0);
+        if (j < p) {
+            const T vv = vtv[j];
+            if (vv > T(0)) {
+                T v0 = (lane > j) ? rrow[j] : ((lane == j) ? vhead[j] : T(0));
+                T v1 = (j < p && h1) ? B[j * q + lane + 32] : T(0);
+                const T d = warp_sum_t(v0 * r0 + v1 * r1);
+                const T f = d * (T(2) / vv);
+                r0 -= f * v0;
+                r1 -= f * v1;
+            }
+        }
+    }
+    T x = T(0);
+#pragma unroll
+    for (int i = kSmallP - 1; i >= 0; --i) {
+        if (i < p) {
+            const T di = __shfl_sync(0xffffffffu, rrow[i], i);
+            const T yi = __shfl_sync(0xffffffffu, r0, i);
+            const T xi = (fabs(di) <= small) ? T(0) : yi / di;
+            if (lane == i) x = xi;
+            if (lane < i) r0 -= rrow[i] * xi;
+        }
+    }
+    if (lane < p) rhs[lane] = x;
+    __syncwarp();
+}
+
+// Bitonic sort of buf[0..len) on one warp in registers, E elements per lane
+// (element e = r*32 + lane); len <= 32*E.  Ascending, padded with INT32_MAX.
+template <int E>
+__device__ void warp_sort_regs(int32_t *buf, int len) {
+    const int lane = threadIdx.x & 31;
+    int32_t x[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        int e = r * 32 + lane;
+        x[r] = (e < len) ? buf[e] : INT32_MAX;
+    }
+    constexpr int N = 32 * E;
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int jr = j >> 5;
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const int rp = r ^ jr;
+                    if (rp > r) {
+                        const bool up = ((r * 32) & k) == 0;
+                        int32_t a = x[r], b = x[rp];
+                        if ((a > b) == up) { x[r] = b; x[rp] = a; }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const int e = r * 32 + lane;
+                    const int32_t other = __shfl_xor_sync(0xffffffffu, x[r], j);
+                    const bool up = (e & k) == 0;
+                    const bool lower = (lane & j) == 0;
+                    // lower element of an ascending pair keeps the min
+                    const bool keep_min = (lower == up);
+                    x[r] = keep_min ? min(x[r], other) : max(x[r], other);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < E; ++r) buf[r * 32 + lane] = x[r];
+    __syncwarp();
+}
+
+}  // namespace rsai
