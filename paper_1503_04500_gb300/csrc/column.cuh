@@ -113,6 +113,88 @@ __device__ __forceinline__ long long solve_flops(long long q0, long long p0, lon
     return f + p * p;
 }
 
+// rhs[0..p) <- R^{-1} rhs[0..p) (column-oriented, in place)
+template <class Team, typename T>
+__device__ void back_substitute_team(const Team &team, const T *B, int q, int p, T *rhs, T small) {
+    const int me = team.rank();
+    for (int i = p - 1; i >= 0; --i) {
+        T d = B[(int64_t)i * q + i];
+        T xi = (fabs(d) <= small) ? T(0) : rhs[i] / d;
+        team.sync();
+        for (int c = me; c < i; c += Team::SIZE) rhs[c] -= B[(int64_t)i * q + c] * xi;
+        if (me == 0) rhs[i] = xi;
+        team.sync();
+    }
+}
+
+// Householder QR of B (q x p, column-major, ld q) applied to rhs, then back
+// substitution into rhs[0..p).  Keeps the reflectors (v_j below the diagonal
+// of B, heads in vhead, v^T v in vtv) for the refinement solve.  Returns the
+// rank flag.  Team-generic (rows strided over the team, one team reduction per
+// trailing column); not inlined.
+template <class Team, typename T>
+__device__ __noinline__ int qr_solve_team(Team team, T *B, int q, int p, T *rhs, T *vhead, T *vtvs, T small) {
+    const int me = team.rank();
+    int rank_flag = 0;
+    for (int j = 0; j < p; ++j) {
+        T *col = B + (int64_t)j * q;
+        T part = 0;
+        for (int i = me; i < q; i += Team::SIZE)
+            if (i >= j) part += col[i] * col[i];
+        T sigma = team.sum(part);
+        T x0 = col[j];
+        T nrm = sqrt(sigma);
+        T alpha = (x0 >= T(0)) ? -nrm : nrm;
+        T v0 = x0 - alpha;
+        T vtv = sigma - x0 * x0 + v0 * v0;
+        if (vtv > T(0)) {
+            const T two_over = T(2) / vtv;
+            for (int c = j + 1; c <= p; ++c) {
+                T *t = (c < p) ? B + (int64_t)c * q : rhs;
+                T d = 0;
+                for (int i = me; i < q; i += Team::SIZE)
+                    if (i >= j) d += ((i == j) ? v0 : col[i]) * t[i];
+                T sdot = team.sum(d);
+                T f = sdot * two_over;
+                for (int i = me; i < q; i += Team::SIZE)
+                    if (i >= j) t[i] -= f * ((i == j) ? v0 : col[i]);
+            }
+        }
+        team.sync();
+        if (me == 0) {
+            col[j] = alpha;
+            vhead[j] = v0;
+            vtvs[j] = vtv;
+        }
+        rank_flag |= (fabs(alpha) <= small) ? 1 : 0;
+        team.sync();
+    }
+    back_substitute_team(team, B, q, p, rhs, small);
+    return rank_flag;
+}
+
+// rhs <- Q^T rhs with the stored reflectors, then R^{-1}; not inlined
+template <class Team, typename T>
+__device__ __noinline__ void apply_qt_team(Team team, const T *B, int q, int p, T *rhs, const T *vhead,
+                                           const T *vtvs, T small) {
+    const int me = team.rank();
+    for (int j = 0; j < p; ++j) {
+        const T *col = B + (int64_t)j * q;
+        T v0 = vhead[j], vtv = vtvs[j];
+        if (vtv > T(0)) {
+            T d = 0;
+            for (int i = me; i < q; i += Team::SIZE)
+                if (i >= j) d += ((i == j) ? v0 : col[i]) * rhs[i];
+            T sdot = team.sum(d);
+            T f = sdot * (T(2) / vtv);
+            for (int i = me; i < q; i += Team::SIZE)
+                if (i >= j) rhs[i] -= f * ((i == j) ? v0 : col[i]);
+        }
+        team.sync();
+    }
+    back_substitute_team(team, B, q, p, rhs, small);
+}
+
 template <class Team, typename T> struct Column {
     const Team &team;
     const DevA &A;
@@ -166,8 +248,7 @@ template <class Team, typename T> struct Column {
     }
 
     // Householder QR of B (q x p, ld q) applied to rhs, then back substitution
-    // into rhs[0..p).  Keeps the reflectors (v_j below the diagonal of B,
-    // heads in vhead, v^T v in vtv) for the refinement solve.
+    // into rhs[0..p); the reflectors stay in B (tails), vhead and vtv.
     __device__ void qr_solve(T small) {
         if constexpr (std::is_same<Team, WarpTeam>::value) {
             if (p <= kSmallP && q <= kSmallQ) {
@@ -175,58 +256,10 @@ template <class Team, typename T> struct Column {
                 return;
             }
         }
-        const int me = team.rank();
-        for (int j = 0; j < p; ++j) {
-            T *col = w.B + (int64_t)j * q;
-            T part = 0;
-            for (int i = me; i < q; i += Team::SIZE)
-                if (i >= j) part += col[i] * col[i];
-            T sigma = team.sum(part);
-            T x0 = col[j];
-            T nrm = sqrt(sigma);
-            T alpha = (x0 >= T(0)) ? -nrm : nrm;
-            T v0 = x0 - alpha;
-            T vtv = sigma - x0 * x0 + v0 * v0;
-            if (vtv > T(0)) {
-                const T two_over = T(2) / vtv;
-                for (int c = j + 1; c <= p; ++c) {
-                    T *t = (c < p) ? w.B + (int64_t)c * q : w.rhs;
-                    T d = 0;
-                    for (int i = me; i < q; i += Team::SIZE)
-                        if (i >= j) d += ((i == j) ? v0 : col[i]) * t[i];
-                    T sdot = team.sum(d);
-                    T f = sdot * two_over;
-                    for (int i = me; i < q; i += Team::SIZE)
-                        if (i >= j) t[i] -= f * ((i == j) ? v0 : col[i]);
-                }
-            }
-            team.sync();
-            if (me == 0) {
-                col[j] = alpha;
-                w.vhead[j] = v0;
-                w.vtv[j] = vtv;
-                if (fabs(alpha) <= small) rank_flag = 1;
-            }
-            team.sync();
-        }
-        rank_flag = team.maxv(rank_flag);
-        back_substitute(small);
+        rank_flag = qr_solve_team<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.vtv, small);
     }
 
-    // rhs[0..p) <- R^{-1} rhs[0..p) (column-oriented, in place)
-    __device__ void back_substitute(T small) {
-        const int me = team.rank();
-        for (int i = p - 1; i >= 0; --i) {
-            T d = w.B[(int64_t)i * q + i];
-            T xi = (fabs(d) <= small) ? T(0) : w.rhs[i] / d;
-            team.sync();
-            for (int c = me; c < i; c += Team::SIZE) w.rhs[c] -= w.B[(int64_t)i * q + c] * xi;
-            if (me == 0) w.rhs[i] = xi;
-            team.sync();
-        }
-    }
-
-    // rhs <- Q^T rhs with the stored reflectors, then R^{-1}
+    // rhs <- R^{-1} Q^T rhs with the stored reflectors
     __device__ void apply_qt_solve(T small) {
         if constexpr (std::is_same<Team, WarpTeam>::value) {
             if (p <= kSmallP && q <= kSmallQ) {
@@ -234,22 +267,7 @@ template <class Team, typename T> struct Column {
                 return;
             }
         }
-        const int me = team.rank();
-        for (int j = 0; j < p; ++j) {
-            const T *col = w.B + (int64_t)j * q;
-            T v0 = w.vhead[j], vtv = w.vtv[j];
-            if (vtv > T(0)) {
-                T d = 0;
-                for (int i = me; i < q; i += Team::SIZE)
-                    if (i >= j) d += ((i == j) ? v0 : col[i]) * w.rhs[i];
-                T sdot = team.sum(d);
-                T f = sdot * (T(2) / vtv);
-                for (int i = me; i < q; i += Team::SIZE)
-                    if (i >= j) w.rhs[i] -= f * ((i == j) ? v0 : col[i]);
-            }
-            team.sync();
-        }
-        back_substitute(small);
+        apply_qt_team<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.vtv, small);
     }
 
     // S = I u {k}; r = A(:,J) m - e_k on S in double (Eq. 2.4), row by row

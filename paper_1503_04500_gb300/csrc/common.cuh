@@ -228,7 +228,7 @@ template <int NT> struct BlockTeam {
 // Bitonic sort of buf[0..len) ascending in shared memory; buf must have room
 // for the next power of two (padded with INT32_MAX).
 template <class Team>
-__device__ void team_sort_i32_smem(const Team &team, int32_t *buf, int len) {
+__device__ __noinline__ void team_sort_i32_smem(Team team, int32_t *buf, int len) {
     int N = 1;
     while (N < len) N <<= 1;
     for (int i = len + team.rank(); i < N; i += Team::SIZE) buf[i] = INT32_MAX;

@@ -26,8 +26,13 @@ template <typename T> __device__ __forceinline__ T warp_sum_t(T x) {
 
 // Householder QR of B (q x p, ld q) applied to rhs, then back substitution into
 // rhs[0..p).  vhead/vtv receive v_j(j) and v_j^T v_j.  Returns the rank flag.
+//
+// Columns p..15 are zero-filled, so every operation on them is a no-op: the
+// unrolled loops run branch-free over all 16 slots; only the steps j >= p are
+// skipped.  Not inlined: the unrolled body is large and the column algorithm
+// calls the solve from several places.
 template <typename T>
-__device__ int warp_qr_small(T *B, int q, int p, T *rhs, T *vhead, T *vtv, T small) {
+__device__ __noinline__ int warp_qr_small(T *B, int q, int p, T *rhs, T *vhead, T *vtv, T small) {
     const int lane = threadIdx.x & 31;
     const bool h0 = lane < q, h1 = lane + 32 < q;
     T b0[kSmallP], b1[kSmallP];
@@ -52,25 +57,22 @@ __device__ int warp_qr_small(T *B, int q, int p, T *rhs, T *vhead, T *vtv, T sma
             const T vh = x0 - alpha;
             const T vv = sigma - x0 * x0 + vh * vh;
             if (lane == j) v0 = vh;
-            if (vv > T(0)) {
-                const T two_over = T(2) / vv;
+            {
+                const T two_over = (vv > T(0)) ? T(2) / vv : T(0);
                 T d[kSmallP + 1];
 #pragma unroll
-                for (int c = j + 1; c < kSmallP; ++c) d[c] = (c < p) ? v0 * b0[c] + v1 * b1[c] : T(0);
+                for (int c = j + 1; c < kSmallP; ++c) d[c] = v0 * b0[c] + v1 * b1[c];
                 d[kSmallP] = v0 * r0 + v1 * r1;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-                    for (int c = j + 1; c <= kSmallP; ++c)
-                        if (c == kSmallP || c < p) d[c] += __shfl_xor_sync(0xffffffffu, d[c], o);
+                    for (int c = j + 1; c <= kSmallP; ++c) d[c] += __shfl_xor_sync(0xffffffffu, d[c], o);
                 }
 #pragma unroll
                 for (int c = j + 1; c < kSmallP; ++c) {
-                    if (c < p) {
-                        const T f = d[c] * two_over;
-                        b0[c] -= f * v0;
-                        b1[c] -= f * v1;
-                    }
+                    const T f = d[c] * two_over;
+                    b0[c] -= f * v0;
+                    b1[c] -= f * v1;
                 }
                 const T fr = d[kSmallP] * two_over;
                 r0 -= fr * v0;
@@ -88,13 +90,12 @@ __device__ int warp_qr_small(T *B, int q, int p, T *rhs, T *vhead, T *vtv, T sma
     T x = T(0);
 #pragma unroll
     for (int i = kSmallP - 1; i >= 0; --i) {
-        if (i < p) {
-            const T di = __shfl_sync(0xffffffffu, b0[i], i);
-            const T yi = __shfl_sync(0xffffffffu, r0, i);
-            const T xi = (fabs(di) <= small) ? T(0) : yi / di;
-            if (lane == i) x = xi;
-            if (lane < i) r0 -= b0[i] * xi;
-        }
+        // R_ii = 0 for the empty slots i >= p, which then give x_i = 0
+        const T di = __shfl_sync(0xffffffffu, b0[i], i);
+        const T yi = __shfl_sync(0xffffffffu, r0, i);
+        const T xi = (fabs(di) <= small) ? T(0) : yi / di;
+        if (lane == i) x = xi;
+        if (lane < i) r0 -= b0[i] * xi;
     }
 #pragma unroll
     for (int c = 0; c < kSmallP; ++c) {
@@ -110,7 +111,8 @@ __device__ int warp_qr_small(T *B, int q, int p, T *rhs, T *vhead, T *vtv, T sma
 
 // rhs <- R^{-1} Q^T rhs with the reflectors left in B by warp_qr_small
 template <typename T>
-__device__ void warp_apply_qt_small(const T *B, int q, int p, T *rhs, const T *vhead, const T *vtv, T small) {
+__device__ __noinline__ void warp_apply_qt_small(const T *B, int q, int p, T *rhs, const T *vhead, const T *vtv,
+                                                 T small) {
     const int lane = threadIdx.x & 31;
     const bool h0 = lane < q, h1 = lane + 32 < q;
     T r0 = h0 ? rhs[lane] : T(0);
@@ -118,29 +120,25 @@ __device__ void warp_apply_qt_small(const T *B, int q, int p, T *rhs, const T *v
     T rrow[kSmallP];  // row `lane` of R (for the back substitution)
 #pragma unroll
     for (int j = 0; j < kSmallP; ++j) {
-        rrow[j] = (j < p && h0) ? B[j * q + lane] : T(0);
-        if (j < p) {
-            const T vv = vtv[j];
-            if (vv > T(0)) {
-                T v0 = (lane > j) ? rrow[j] : ((lane == j) ? vhead[j] : T(0));
-                T v1 = (j < p && h1) ? B[j * q + lane + 32] : T(0);
-                const T d = warp_sum_t(v0 * r0 + v1 * r1);
-                const T f = d * (T(2) / vv);
-                r0 -= f * v0;
-                r1 -= f * v1;
-            }
-        }
+        const bool live = j < p;
+        rrow[j] = (live && h0) ? B[j * q + lane] : T(0);
+        const T vv = live ? vtv[j] : T(0);
+        const T vh = live ? vhead[j] : T(0);
+        T v0 = (lane > j) ? rrow[j] : ((lane == j) ? vh : T(0));
+        T v1 = (live && h1) ? B[j * q + lane + 32] : T(0);
+        const T d = warp_sum_t(v0 * r0 + v1 * r1);
+        const T f = (vv > T(0)) ? d * (T(2) / vv) : T(0);
+        r0 -= f * v0;
+        r1 -= f * v1;
     }
     T x = T(0);
 #pragma unroll
     for (int i = kSmallP - 1; i >= 0; --i) {
-        if (i < p) {
-            const T di = __shfl_sync(0xffffffffu, rrow[i], i);
-            const T yi = __shfl_sync(0xffffffffu, r0, i);
-            const T xi = (fabs(di) <= small) ? T(0) : yi / di;
-            if (lane == i) x = xi;
-            if (lane < i) r0 -= rrow[i] * xi;
-        }
+        const T di = __shfl_sync(0xffffffffu, rrow[i], i);
+        const T yi = __shfl_sync(0xffffffffu, r0, i);
+        const T xi = (fabs(di) <= small) ? T(0) : yi / di;
+        if (lane == i) x = xi;
+        if (lane < i) r0 -= rrow[i] * xi;
     }
     if (lane < p) rhs[lane] = x;
     __syncwarp();
@@ -149,7 +147,7 @@ __device__ void warp_apply_qt_small(const T *B, int q, int p, T *rhs, const T *v
 // Bitonic sort of buf[0..len) on one warp in registers, E elements per lane
 // (element e = r*32 + lane); len <= 32*E.  Ascending, padded with INT32_MAX.
 template <int E>
-__device__ void warp_sort_regs(int32_t *buf, int len) {
+__device__ __noinline__ void warp_sort_regs(int32_t *buf, int len) {
     const int lane = threadIdx.x & 31;
     int32_t x[E];
 #pragma unroll
