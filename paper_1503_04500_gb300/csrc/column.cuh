@@ -35,13 +35,14 @@ struct Caps {
     int scap;      // sort buffer (power of two)
     int rcap;      // max |R| (dominant rows used so far)
     int64_t bcap;  // max q*p elements of B
+    int hcap;      // slots of the J -> position hash (power of two >= 2*pcap), 0 = none
 };
 
 template <typename T> struct Work {
     T *B, *vhead, *vtv, *rhs;
     double *m, *r;
     long long *ctr;
-    int32_t *I, *S, *J, *Jn, *Rset, *buf, *buf2, *Rhat;
+    int32_t *I, *S, *J, *Jn, *Rset, *buf, *buf2, *Rhat, *hkey, *hval;
 
     __host__ __device__ static size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
     __host__ __device__ static size_t bytes(const Caps &c) {
@@ -58,6 +59,7 @@ template <typename T> struct Work {
         b += align16(sizeof(int32_t) * (size_t)c.rcap);
         b += 2 * align16(sizeof(int32_t) * (size_t)c.scap);
         b += align16(sizeof(int32_t) * 32);
+        b += 2 * align16(sizeof(int32_t) * (size_t)c.hcap);
         return b;
     }
     __device__ void carve(char *base, const Caps &c) {
@@ -77,6 +79,8 @@ template <typename T> struct Work {
         buf = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.scap);
         buf2 = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.scap);
         Rhat = (int32_t *)(base + o); o += align16(sizeof(int32_t) * 32);
+        hkey = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.hcap);
+        hval = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.hcap);
     }
 };
 
@@ -213,6 +217,39 @@ template <class Team, typename T> struct Column {
     __device__ Column(const Team &t, const DevA &a, const DevParams &pp, const Caps &c, Work<T> &ww, int32_t kk)
         : team(t), A(a), P(pp), cap(c), w(ww), k(kk) {}
 
+    // J -> position in J: open-addressing hash (warp bins) or binary search.
+    // The table's layout may depend on insertion order; lookups do not.
+    __device__ __forceinline__ unsigned hslot(int32_t col) const {
+        return ((unsigned)col * 0x9E3779B1u) >> (32 - __ffs(cap.hcap) + 1);
+    }
+    __device__ void build_jhash() {
+        if (cap.hcap == 0) return;
+        for (int i = team.rank(); i < cap.hcap; i += Team::SIZE) w.hkey[i] = -1;
+        team.sync();
+        const unsigned mask = (unsigned)cap.hcap - 1;
+        for (int c = team.rank(); c < p; c += Team::SIZE) {
+            const int32_t key = w.J[c];
+            unsigned sl = hslot(key);
+            for (;;) {
+                int32_t old = atomicCAS(&w.hkey[sl], -1, key);
+                if (old == -1) { w.hval[sl] = c; break; }
+                sl = (sl + 1) & mask;
+            }
+        }
+        team.sync();
+    }
+    __device__ __forceinline__ int find_J(int32_t col) const {
+        if (cap.hcap == 0) return find_i32(w.J, p, col);
+        const unsigned mask = (unsigned)cap.hcap - 1;
+        unsigned sl = hslot(col);
+        for (;;) {
+            int32_t key = w.hkey[sl];
+            if (key == col) return w.hval[sl];
+            if (key == -1) return -1;
+            sl = (sl + 1) & mask;
+        }
+    }
+
     // I = sorted rows of A(:,J) (Section 2).  Returns false on overflow.
     __device__ bool rows_of_J() {
         int base = 0;
@@ -251,7 +288,7 @@ template <class Team, typename T> struct Column {
     // into rhs[0..p); the reflectors stay in B (tails), vhead and vtv.
     __device__ void qr_solve(T small) {
         if constexpr (std::is_same<Team, WarpTeam>::value) {
-            if (p <= kSmallP && q <= kSmallQ) {
+            if (p > 2 && p <= kSmallP && q <= kSmallQ) {
                 rank_flag = warp_qr_small(w.B, q, p, w.rhs, w.vhead, w.vtv, small);
                 return;
             }
@@ -262,7 +299,7 @@ template <class Team, typename T> struct Column {
     // rhs <- R^{-1} Q^T rhs with the stored reflectors
     __device__ void apply_qt_solve(T small) {
         if constexpr (std::is_same<Team, WarpTeam>::value) {
-            if (p <= kSmallP && q <= kSmallQ) {
+            if (p > 2 && p <= kSmallP && q <= kSmallQ) {
                 warp_apply_qt_small(w.B, q, p, w.rhs, w.vhead, w.vtv, small);
                 return;
             }
@@ -301,7 +338,7 @@ template <class Team, typename T> struct Column {
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    int pos = (cj[u] >= 0) ? find_i32(w.J, p, cj[u]) : -1;
+                    int pos = (cj[u] >= 0) ? find_J(cj[u]) : -1;
                     if (pos >= 0) { acc = fma(av[u], w.m[pos], acc); ++cnt; }
                 }
             }
@@ -320,6 +357,7 @@ template <class Team, typename T> struct Column {
     // previously solved J (the paper's QR update; counted as such).
     __device__ bool solve(bool append) {
         const int me = team.rank();
+        build_jhash();
         if (!rows_of_J()) return false;
         if ((int64_t)q * p > cap.bcap) return false;
         // B = A(I,J), zero-filled
@@ -328,24 +366,51 @@ template <class Team, typename T> struct Column {
         for (int i = me; i < q; i += Team::SIZE) w.rhs[i] = (w.I[i] == k) ? T(1) : T(0);
         team.sync();
         T fro2 = 0;
-        for (int c = me; c < p; c += Team::SIZE) {
-            const int32_t j = w.J[c];
-            const int64_t e0 = A.col_ptr[j], e1 = A.col_ptr[j + 1];
-            T *Bc = w.B + (int64_t)c * q;
-            for (int64_t e = e0; e < e1; e += 4) {
-                int32_t ri[4];
-                double av[4];
+        if (cap.hcap) {
+            // row by row: row I[i] of A restricted to the columns in J
+            for (int i = me; i < q; i += Team::SIZE) {
+                const int32_t row = w.I[i];
+                const int64_t e0 = A.row_ptr[row], e1 = A.row_ptr[row + 1];
+                for (int64_t e = e0; e < e1; e += 4) {
+                    int32_t cj[4];
+                    double av[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    ri[u] = (e + u < e1) ? A.row_idx[e + u] : -1;
-                    av[u] = (e + u < e1) ? A.cval[e + u] : 0.0;
+                    for (int u = 0; u < 4; ++u) {
+                        cj[u] = (e + u < e1) ? A.col_idx[e + u] : -1;
+                        av[u] = (e + u < e1) ? A.val[e + u] : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int c = (cj[u] >= 0) ? find_J(cj[u]) : -1;
+                        if (c >= 0) {
+                            const T a = (T)av[u];
+                            w.B[(int64_t)c * q + i] = a;
+                            fro2 += a * a;
+                        }
+                    }
                 }
+            }
+        } else {
+            // column by column: column J[c] of A placed by the position of its rows in I
+            for (int c = me; c < p; c += Team::SIZE) {
+                const int32_t j = w.J[c];
+                const int64_t e0 = A.col_ptr[j], e1 = A.col_ptr[j + 1];
+                T *Bc = w.B + (int64_t)c * q;
+                for (int64_t e = e0; e < e1; e += 4) {
+                    int32_t ri[4];
+                    double av[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (ri[u] >= 0) {
-                        T a = (T)av[u];
-                        Bc[find_i32(w.I, q, ri[u])] = a;
-                        fro2 += a * a;
+                    for (int u = 0; u < 4; ++u) {
+                        ri[u] = (e + u < e1) ? A.row_idx[e + u] : -1;
+                        av[u] = (e + u < e1) ? A.cval[e + u] : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (ri[u] >= 0) {
+                            T a = (T)av[u];
+                            Bc[find_i32(w.I, q, ri[u])] = a;
+                            fro2 += a * a;
+                        }
                     }
                 }
             }
@@ -552,7 +617,7 @@ template <class Team, typename T> struct Column {
         int base = 0;
         for (int i0 = 0; i0 < nu; i0 += Team::SIZE) {
             int i = i0 + me;
-            int f = (i < nu) && (find_i32(w.J, p, w.buf2[i]) < 0);
+            int f = (i < nu) && (find_J(w.buf2[i]) < 0);
             int t2;
             int pos = team.scan(f, &t2);
             if (f) w.buf[base + pos] = w.buf2[i];

@@ -193,12 +193,12 @@ int plan_bins(rsai_handle *h) {
     int dev = h->device, max_optin = 0;
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int rneed = std::max(64, h->params.c * std::max(1, h->params.l_max));
-    h->capW = Caps{64, 32, 256, 64, 64 * 32};
+    h->capW = Caps{64, 32, 256, 64, 64 * 32, 64};
     int occ = occupancy_bin_warp(fp32, kWarpsPerCta, h->capW);
     if (occ < 1) return RSAI_ERR_CUDA;
     h->grid_w = h->sms * occ;
     // bin C: shared-memory workspace as large as the opt-in limit allows
-    Caps c{1024, 256, 4096, std::min(rneed * 2, 2048), 0};
+    Caps c{1024, 256, 4096, std::min(rneed * 2, 2048), 0, 0};
     size_t base = fp32 ? work_bytes<float>(c) : work_bytes<double>(c);
     size_t avail = (size_t)max_optin - 2048;
     if (base >= avail) return RSAI_ERR_CUDA;
@@ -208,7 +208,7 @@ int plan_bins(rsai_handle *h) {
     if (occ < 1) return RSAI_ERR_CUDA;
     h->grid_c = h->sms * occ;
     // bin G: a global-memory slab per CTA, one CTA per SM
-    h->capG = Caps{32768, 4096, 131072, 8192, (int64_t)1 << 22};
+    h->capG = Caps{32768, 4096, 131072, 8192, (int64_t)1 << 22, 0};
     h->gstride = ((fp32 ? work_bytes<float>(h->capG) : work_bytes<double>(h->capG)) + 255) & ~size_t(255);
     h->grid_g = std::min(h->sms, 8);  // grown after the first build if the tail needs it
     return RSAI_OK;

@@ -90,12 +90,13 @@ __device__ __noinline__ int warp_qr_small(T *B, int q, int p, T *rhs, T *vhead, 
     T x = T(0);
 #pragma unroll
     for (int i = kSmallP - 1; i >= 0; --i) {
-        // R_ii = 0 for the empty slots i >= p, which then give x_i = 0
-        const T di = __shfl_sync(0xffffffffu, b0[i], i);
-        const T yi = __shfl_sync(0xffffffffu, r0, i);
-        const T xi = (fabs(di) <= small) ? T(0) : yi / di;
-        if (lane == i) x = xi;
-        if (lane < i) r0 -= b0[i] * xi;
+        if (i < p) {
+            const T di = __shfl_sync(0xffffffffu, b0[i], i);
+            const T yi = __shfl_sync(0xffffffffu, r0, i);
+            const T xi = (fabs(di) <= small) ? T(0) : yi / di;
+            if (lane == i) x = xi;
+            if (lane < i) r0 -= b0[i] * xi;
+        }
     }
 #pragma unroll
     for (int c = 0; c < kSmallP; ++c) {
@@ -134,11 +135,13 @@ __device__ __noinline__ void warp_apply_qt_small(const T *B, int q, int p, T *rh
     T x = T(0);
 #pragma unroll
     for (int i = kSmallP - 1; i >= 0; --i) {
-        const T di = __shfl_sync(0xffffffffu, rrow[i], i);
-        const T yi = __shfl_sync(0xffffffffu, r0, i);
-        const T xi = (fabs(di) <= small) ? T(0) : yi / di;
-        if (lane == i) x = xi;
-        if (lane < i) r0 -= rrow[i] * xi;
+        if (i < p) {
+            const T di = __shfl_sync(0xffffffffu, rrow[i], i);
+            const T yi = __shfl_sync(0xffffffffu, r0, i);
+            const T xi = (fabs(di) <= small) ? T(0) : yi / di;
+            if (lane == i) x = xi;
+            if (lane < i) r0 -= rrow[i] * xi;
+        }
     }
     if (lane < p) rhs[lane] = x;
     __syncwarp();
