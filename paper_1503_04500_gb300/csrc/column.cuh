@@ -454,8 +454,9 @@ template <class Team, typename T> struct Column {
 
     // Eq. 4.3: drop |m_j| <= tau, keep at least the largest, re-solve once.
     // Magnitudes are compared as ordered integer keys (exact).
+    // Returns true if J lost entries (the caller re-solves once).
     __device__ bool drop() {
-        if (P.drop_mode == RSAI_DROP_NONE) return true;
+        if (P.drop_mode == RSAI_DROP_NONE) return false;
         const int me = team.rank();
         const double tau = (P.drop_mode == RSAI_DROP_ADAPTIVE) ? P.eps / ((double)p * *P.norm1) : *P.tau_fixed;
         const long long tk = abskey(tau);
@@ -468,10 +469,10 @@ template <class Team, typename T> struct Column {
             if (dom_before(a, c, ba, bi)) { ba = a; bi = c; }
         }
         const int keep_total = team.sum(nkeep);
-        if (keep_total == p) return true;
+        if (keep_total == p) return false;
         if (keep_total == 0) {
             team.argmax(ba, bi);
-            if (p == 1) return true;
+            if (p == 1) return false;
             int32_t jb = w.J[bi];
             team.sync();
             if (me == 0) w.J[0] = jb;
@@ -493,7 +494,7 @@ template <class Team, typename T> struct Column {
             team.sync();
         }
         c_drops += 1;
-        return solve(false);
+        return true;
     }
 
     // Top-c dominant rows of S \ R (Algorithm 1 step 4) into w.Rhat; returns
@@ -659,27 +660,37 @@ template <class Team, typename T> struct Column {
         if (me == 0) w.J[0] = k;
         team.sync();
         c_bytes += 12 * (A.col_ptr[k + 1] - A.col_ptr[k]) + 16;
-        if (!solve(false)) return COL_OVERFLOW;
-        if (!drop()) return COL_OVERFLOW;
-        residual();
-        while (rho > P.eps && l < P.l_max) {
-            int nh = dominant_rows();
-            if (nh == 0) break;
-            if (!add_to_R(nh)) return COL_OVERFLOW;
-            {
-                long long b = 0;
-                if (me < nh) b = 4 * (A.row_ptr[w.Rhat[me] + 1] - A.row_ptr[w.Rhat[me]]) + 16;
-                c_bytes += team.sum(b);
+        // One solve site: the first pass of every round solves on the new J
+        // (appended to the last factor after the first round), the second
+        // re-solves after a drop (Eq. 4.3); then the residual (Eq. 2.4).
+        bool append = false;
+        for (;;) {
+            for (int pass = 0; pass < 2; ++pass) {
+                if (!solve(append)) return COL_OVERFLOW;
+                append = false;
+                if (pass == 1 || !drop()) break;
             }
-            int nj = new_columns(nh);
-            if (nj < 0) return COL_OVERFLOW;
-            ++l;
-            if (nj == 0) continue;
-            note_bytes_columns(0, nj, w.buf);
-            if (!merge_J(nj)) return COL_OVERFLOW;
-            if (!solve(true)) return COL_OVERFLOW;
-            if (!drop()) return COL_OVERFLOW;
             residual();
+            bool grown = false;
+            while (!grown && rho > P.eps && l < P.l_max) {
+                int nh = dominant_rows();
+                if (nh == 0) break;
+                if (!add_to_R(nh)) return COL_OVERFLOW;
+                {
+                    long long b = 0;
+                    if (me < nh) b = 4 * (A.row_ptr[w.Rhat[me] + 1] - A.row_ptr[w.Rhat[me]]) + 16;
+                    c_bytes += team.sum(b);
+                }
+                int nj = new_columns(nh);
+                if (nj < 0) return COL_OVERFLOW;
+                ++l;
+                if (nj == 0) continue;  // Algorithm 1 step 6: next dominant rows
+                note_bytes_columns(0, nj, w.buf);
+                if (!merge_J(nj)) return COL_OVERFLOW;
+                grown = true;
+            }
+            if (!grown) break;
+            append = true;
         }
         c_bytes += 36LL * p;
         return COL_DONE;
