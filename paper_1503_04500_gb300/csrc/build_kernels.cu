@@ -129,6 +129,7 @@ __device__ void emit_or_forward(const Team &team, Column<Team, T> &col, int st, 
                     (fin ? 0 : RSAI_COL_NONFINITE);
         O.col_off[k] = (int64_t)off;
         O.col_len[k] = p;
+        O.col_q[k] = col.q;
         O.rho[k] = col.rho;
         O.loops[k] = col.l;
         O.flags[k] = flags;
@@ -150,9 +151,24 @@ __device__ void emit_or_forward(const Team &team, Column<Team, T> &col, int st, 
     (void)bin;
 }
 
-template <class Team, typename T>
+// A frozen-pattern column that does not fit this bin: forward or fail
+__device__ __forceinline__ void forward_frozen(int me, const ColQueue &Q, const ColOut &O, int32_t k,
+                                               bool last_bin, long long *ctr) {
+    if (me != 0) return;
+    if (!last_bin) {
+        uint32_t pos = atomicAdd(Q.ovf_count, 1u);
+        if ((int64_t)pos < Q.ovf_cap) Q.ovf_cols[pos] = k;
+        else set_error(O.err, RSAI_ERR_WORKSPACE);
+    } else {
+        ctr[CTR_FAILED] += 1;
+        set_error(O.err, RSAI_ERR_WORKSPACE);
+    }
+}
+
+template <int MODE, class Team, typename T>
 __device__ void run_queue(const Team &team, Work<T> &w, const DevA &A, const DevParams &P, const Caps &cap,
-                          const ColQueue &Q, const ColOut &O, unsigned long long *gctr, bool last_bin, int bin) {
+                          const ColQueue &Q, const ColOut &O, const Frozen &F, unsigned long long *gctr,
+                          bool last_bin, int bin) {
     const int me = team.rank();
     for (int i = me; i < CTR_COUNT; i += Team::SIZE) w.ctr[i] = 0;
     team.sync();
@@ -164,8 +180,28 @@ __device__ void run_queue(const Team &team, Work<T> &w, const DevA &A, const Dev
         if ((int64_t)idx >= nq) break;
         int32_t k = Q.cols ? Q.cols[idx] : (int32_t)idx;
         Column<Team, T> col(team, A, P, cap, w, k);
-        int st = col.run();
-        emit_or_forward(team, col, st, Q, O, last_bin, bin);
+        if constexpr (MODE == MODE_BUILD) {
+            int st = col.run();
+            emit_or_forward(team, col, st, Q, O, last_bin, bin);
+        } else {
+            const int64_t mo = F.Mcolptr[k];
+            const int pk = (int)(F.Mcolptr[k + 1] - mo);
+            bool ok = col.load_pattern(F.Mrows + mo, pk);
+            if (ok) {
+                if constexpr (MODE == MODE_REFIT) ok = col.refit();
+                else ok = col.adjoint(F);
+            }
+            if (!ok) {
+                forward_frozen(me, Q, O, k, last_bin, w.ctr);
+            } else {
+                if constexpr (MODE == MODE_REFIT) {
+                    for (int c = me; c < pk; c += Team::SIZE) F.Mval_csr[F.Mcsc_to_csr[mo + c]] = w.m[c];
+                    if (me == 0) F.rho2[k] = col.rho * col.rho;
+                }
+                if (me == 0) w.ctr[CTR_COLS] += 1;
+            }
+            team.sync();
+        }
     }
     team.sync();
     if (me == 0) {
@@ -179,22 +215,21 @@ __device__ void run_queue(const Team &team, Work<T> &w, const DevA &A, const Dev
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128, (sizeof(T) == 8 ? 2 : 4)) k_bin_warp(DevA A, DevParams P, Caps cap, ColQueue Q, ColOut O,
-                                                  unsigned long long *gctr,
-                                                  int last_bin) {
+template <typename T, int MODE>
+__global__ void __launch_bounds__(128, (sizeof(T) == 8 ? 2 : 4))
+    k_bin_warp(DevA A, DevParams P, Caps cap, ColQueue Q, ColOut O, Frozen F, unsigned long long *gctr, int last_bin) {
     extern __shared__ __align__(16) char smem[];
     const int wid = threadIdx.x >> 5;
     Work<T> w;
     w.carve(smem + (size_t)wid * Work<T>::bytes(cap), cap);
     WarpTeam team;
-    run_queue(team, w, A, P, cap, Q, O, gctr, last_bin != 0, 0);
+    run_queue<MODE>(team, w, A, P, cap, Q, O, F, gctr, last_bin != 0, 0);
 }
 
-template <typename T, int NT>
-__global__ void __launch_bounds__(NT, 1) k_bin_block(DevA A, DevParams P, Caps cap, ColQueue Q, ColOut O,
-                                                  unsigned long long *gctr,
-                                                  int last_bin, char *gwork, size_t gstride, int bin) {
+template <typename T, int NT, int MODE>
+__global__ void __launch_bounds__(NT, 1)
+    k_bin_block(DevA A, DevParams P, Caps cap, ColQueue Q, ColOut O, Frozen F, unsigned long long *gctr,
+                int last_bin, char *gwork, size_t gstride, int bin) {
     extern __shared__ __align__(16) char smem[];
     __shared__ unsigned long long red[NT / 32 + 1];
     __shared__ int redi[NT / 32 + 1];
@@ -202,7 +237,36 @@ __global__ void __launch_bounds__(NT, 1) k_bin_block(DevA A, DevParams P, Caps c
     if (gwork) w.carve(gwork + (size_t)blockIdx.x * gstride, cap);
     else w.carve(smem, cap);
     BlockTeam<NT> team{red, redi};
-    run_queue(team, w, A, P, cap, Q, O, gctr, last_bin != 0, bin);
+    run_queue<MODE>(team, w, A, P, cap, Q, O, F, gctr, last_bin != 0, bin);
+}
+
+// ---------------------------------------------------------------------------
+// adjoint, second pass: dL/dA(i,j) = sum over the columns k of row j of M of
+//   r_k(i) alpha_k(j) - w_k(i) x_k(j)      (k ascending: fixed order)
+
+__global__ void k_invert_map(const int64_t *map, int64_t n, int64_t *inv) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < n) inv[map[e]] = e;
+}
+
+__global__ void k_adjoint_gather(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const int64_t *Mrowptr,
+                                 const int32_t *Mcols, const int64_t *Mcsr_to_csc, const int64_t *qoff,
+                                 const int32_t *poolI, const double *poolR, const double *poolW,
+                                 const double *alphaM, const double *xM, double *grad) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+        const int32_t j = col_idx[e];
+        double acc = 0.0;
+        for (int64_t f = Mrowptr[j]; f < Mrowptr[j + 1]; ++f) {
+            const int32_t kk = Mcols[f];
+            const int64_t ce = Mcsr_to_csc[f];
+            const int64_t a = qoff[kk];
+            const int pos = find_i32(poolI + a, (int)(qoff[kk + 1] - a), (int32_t)i);
+            if (pos >= 0) acc += poolR[a + pos] * alphaM[ce] - poolW[a + pos] * xM[ce];
+        }
+        grad[e] = acc;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -367,33 +431,63 @@ size_t work_bytes(const Caps &c) { return Work<T>::bytes(c); }
 template size_t work_bytes<float>(const Caps &);
 template size_t work_bytes<double>(const Caps &);
 
-cudaError_t launch_bin_warp(bool fp32, int grid, int warps, const DevA &A, const DevParams &P, const Caps &cap,
-                            const ColQueue &Q, const ColOut &O, unsigned long long *gctr, bool last,
-                            cudaStream_t st) {
-    size_t smem = fp32 ? warp_bin_smem<float>(cap, warps) : warp_bin_smem<double>(cap, warps);
-    if (fp32) {
-        cudaFuncSetAttribute(k_bin_warp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_bin_warp<float><<<grid, warps * 32, smem, st>>>(A, P, cap, Q, O, gctr, last ? 1 : 0);
-    } else {
-        cudaFuncSetAttribute(k_bin_warp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_bin_warp<double><<<grid, warps * 32, smem, st>>>(A, P, cap, Q, O, gctr, last ? 1 : 0);
-    }
+template <typename T, int MODE>
+static cudaError_t launch_warp_t(int grid, int warps, const DevA &A, const DevParams &P, const Caps &cap,
+                                 const ColQueue &Q, const ColOut &O, const Frozen &F, unsigned long long *gctr,
+                                 bool last, cudaStream_t st) {
+    size_t smem = warp_bin_smem<T>(cap, warps);
+    cudaFuncSetAttribute(k_bin_warp<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_bin_warp<T, MODE><<<grid, warps * 32, smem, st>>>(A, P, cap, Q, O, F, gctr, last ? 1 : 0);
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin_block(bool fp32, int grid, const DevA &A, const DevParams &P, const Caps &cap,
-                             const ColQueue &Q, const ColOut &O, unsigned long long *gctr, bool last, char *gwork,
-                             size_t gstride, int bin, cudaStream_t st) {
-    size_t smem = gwork ? 0 : (fp32 ? Work<float>::bytes(cap) : Work<double>::bytes(cap));
+template <typename T, int MODE>
+static cudaError_t launch_block_t(int grid, const DevA &A, const DevParams &P, const Caps &cap, const ColQueue &Q,
+                                  const ColOut &O, const Frozen &F, unsigned long long *gctr, bool last, char *gwork,
+                                  size_t gstride, int bin, cudaStream_t st) {
+    size_t smem = gwork ? 0 : Work<T>::bytes(cap);
+    cudaFuncSetAttribute(k_bin_block<T, kBlockThreads, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_bin_block<T, kBlockThreads, MODE><<<grid, kBlockThreads, smem, st>>>(A, P, cap, Q, O, F, gctr, last ? 1 : 0,
+                                                                          gwork, gstride, bin);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_warp(int mode, bool fp32, int grid, int warps, const DevA &A, const DevParams &P,
+                            const Caps &cap, const ColQueue &Q, const ColOut &O, const Frozen &F,
+                            unsigned long long *gctr, bool last, cudaStream_t st) {
     if (fp32) {
-        cudaFuncSetAttribute(k_bin_block<float, kBlockThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_bin_block<float, kBlockThreads><<<grid, kBlockThreads, smem, st>>>(A, P, cap, Q, O, gctr, last ? 1 : 0,
-                                                                             gwork, gstride, bin);
-    } else {
-        cudaFuncSetAttribute(k_bin_block<double, kBlockThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_bin_block<double, kBlockThreads><<<grid, kBlockThreads, smem, st>>>(A, P, cap, Q, O, gctr, last ? 1 : 0,
-                                                                              gwork, gstride, bin);
+        if (mode == MODE_BUILD) return launch_warp_t<float, MODE_BUILD>(grid, warps, A, P, cap, Q, O, F, gctr, last, st);
+        if (mode == MODE_REFIT) return launch_warp_t<float, MODE_REFIT>(grid, warps, A, P, cap, Q, O, F, gctr, last, st);
+        return launch_warp_t<float, MODE_BACKWARD>(grid, warps, A, P, cap, Q, O, F, gctr, last, st);
     }
+    if (mode == MODE_BUILD) return launch_warp_t<double, MODE_BUILD>(grid, warps, A, P, cap, Q, O, F, gctr, last, st);
+    if (mode == MODE_REFIT) return launch_warp_t<double, MODE_REFIT>(grid, warps, A, P, cap, Q, O, F, gctr, last, st);
+    return launch_warp_t<double, MODE_BACKWARD>(grid, warps, A, P, cap, Q, O, F, gctr, last, st);
+}
+
+cudaError_t launch_bin_block(int mode, bool fp32, int grid, const DevA &A, const DevParams &P, const Caps &cap,
+                             const ColQueue &Q, const ColOut &O, const Frozen &F, unsigned long long *gctr,
+                             bool last, char *gwork, size_t gstride, int bin, cudaStream_t st) {
+#define RSAI_LB(TT, MM) launch_block_t<TT, MM>(grid, A, P, cap, Q, O, F, gctr, last, gwork, gstride, bin, st)
+    if (fp32) {
+        if (mode == MODE_BUILD) return RSAI_LB(float, MODE_BUILD);
+        if (mode == MODE_REFIT) return RSAI_LB(float, MODE_REFIT);
+        return RSAI_LB(float, MODE_BACKWARD);
+    }
+    if (mode == MODE_BUILD) return RSAI_LB(double, MODE_BUILD);
+    if (mode == MODE_REFIT) return RSAI_LB(double, MODE_REFIT);
+    return RSAI_LB(double, MODE_BACKWARD);
+#undef RSAI_LB
+}
+
+cudaError_t launch_adjoint_gather(int64_t n, int64_t nnzM, const int64_t *row_ptr, const int32_t *col_idx,
+                                  const int64_t *Mrowptr, const int32_t *Mcols, const int64_t *Mcsc_to_csr,
+                                  int64_t *Mcsr_to_csc, const int64_t *qoff, const int32_t *poolI,
+                                  const double *poolR, const double *poolW, const double *alphaM,
+                                  const double *xM, double *grad, cudaStream_t st) {
+    if (nnzM > 0) k_invert_map<<<(unsigned)((nnzM + 255) / 256), 256, 0, st>>>(Mcsc_to_csr, nnzM, Mcsr_to_csc);
+    k_adjoint_gather<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, row_ptr, col_idx, Mrowptr, Mcols, Mcsr_to_csc,
+                                                                   qoff, poolI, poolR, poolW, alphaM, xM, grad);
     return cudaGetLastError();
 }
 
@@ -401,11 +495,11 @@ int occupancy_bin_warp(bool fp32, int warps, const Caps &cap) {
     int nb = 0;
     size_t smem = fp32 ? warp_bin_smem<float>(cap, warps) : warp_bin_smem<double>(cap, warps);
     if (fp32) {
-        cudaFuncSetAttribute(k_bin_warp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bin_warp<float>, warps * 32, smem);
+        cudaFuncSetAttribute(k_bin_warp<float, MODE_BUILD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bin_warp<float, MODE_BUILD>, warps * 32, smem);
     } else {
-        cudaFuncSetAttribute(k_bin_warp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bin_warp<double>, warps * 32, smem);
+        cudaFuncSetAttribute(k_bin_warp<double, MODE_BUILD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bin_warp<double, MODE_BUILD>, warps * 32, smem);
     }
     return nb;
 }
@@ -414,11 +508,15 @@ int occupancy_bin_block(bool fp32, const Caps &cap, bool global_work) {
     int nb = 0;
     size_t smem = global_work ? 0 : (fp32 ? Work<float>::bytes(cap) : Work<double>::bytes(cap));
     if (fp32) {
-        cudaFuncSetAttribute(k_bin_block<float, kBlockThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bin_block<float, kBlockThreads>, kBlockThreads, smem);
+        cudaFuncSetAttribute(k_bin_block<float, kBlockThreads, MODE_BUILD>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bin_block<float, kBlockThreads, MODE_BUILD>,
+                                                      kBlockThreads, smem);
     } else {
-        cudaFuncSetAttribute(k_bin_block<double, kBlockThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bin_block<double, kBlockThreads>, kBlockThreads, smem);
+        cudaFuncSetAttribute(k_bin_block<double, kBlockThreads, MODE_BUILD>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bin_block<double, kBlockThreads, MODE_BUILD>,
+                                                      kBlockThreads, smem);
     }
     return nb;
 }

@@ -40,7 +40,7 @@ struct Caps {
 
 template <typename T> struct Work {
     T *B, *vhead, *vtv, *rhs;
-    double *m, *r;
+    double *m, *r, *z, *wv;
     long long *ctr;
     int32_t *I, *S, *J, *Jn, *Rset, *buf, *buf2, *Rhat, *hkey, *hval;
 
@@ -50,6 +50,8 @@ template <typename T> struct Work {
         b += align16(sizeof(T) * (size_t)c.bcap);
         b += 2 * align16(sizeof(T) * (size_t)c.pcap);
         b += align16(sizeof(T) * (size_t)(c.qcap + 1));
+        b += align16(sizeof(double) * (size_t)c.pcap);
+        b += align16(sizeof(double) * (size_t)(c.qcap + 1));
         b += align16(sizeof(double) * (size_t)c.pcap);
         b += align16(sizeof(double) * (size_t)(c.qcap + 1));
         b += align16(sizeof(long long) * CTR_COUNT);
@@ -70,6 +72,8 @@ template <typename T> struct Work {
         rhs = (T *)(base + o); o += align16(sizeof(T) * (size_t)(c.qcap + 1));
         m = (double *)(base + o); o += align16(sizeof(double) * (size_t)c.pcap);
         r = (double *)(base + o); o += align16(sizeof(double) * (size_t)(c.qcap + 1));
+        z = (double *)(base + o); o += align16(sizeof(double) * (size_t)c.pcap);
+        wv = (double *)(base + o); o += align16(sizeof(double) * (size_t)(c.qcap + 1));
         ctr = (long long *)(base + o); o += align16(sizeof(long long) * CTR_COUNT);
         I = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.qcap);
         S = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)(c.qcap + 1));
@@ -210,6 +214,7 @@ template <class Team, typename T> struct Column {
     int64_t q0, p0;
     int rank_flag;
     double rho;
+    T small_last;  // rank threshold of the last solve (reused by the adjoint)
     // per-column work counters (integers; committed only when the column finishes)
     long long c_qr, c_res, c_ref, c_ref64, c_bytes;
     int c_solves, c_drops, c_pmax, c_qmax;
@@ -418,6 +423,7 @@ template <class Team, typename T> struct Column {
         T fro = sqrt(team.sum(fro2));
         team.sync();
         const T small = T(q) * T(2.0 * Unit<T>::u) * fro;
+        small_last = small;
         rank_flag = 0;
         if (q < p) {  // more unknowns than rows: only possible for singular A
             for (int c = me; c < p; c += Team::SIZE) w.m[c] = 0.0;
@@ -652,6 +658,121 @@ template <class Team, typename T> struct Column {
     }
 
     // Runs the whole column.  Returns COL_DONE or COL_OVERFLOW.
+    // ---- frozen pattern (refit, backward) ----
+
+    // J = Jk (sorted, length pk): false if it does not fit this bin
+    __device__ bool load_pattern(const int32_t *Jk, int pk) {
+        p = pk; q = 0; s = 0; nR = 0; l = 0; q0 = 0; p0 = 0; rank_flag = 0; rho = 0.0;
+        c_qr = c_res = c_ref = c_ref64 = c_bytes = 0;
+        c_solves = c_drops = c_pmax = c_qmax = 0;
+        if (pk > cap.pcap || pk < 1) return false;
+        for (int c = team.rank(); c < pk; c += Team::SIZE) w.J[c] = Jk[c];
+        team.sync();
+        return true;
+    }
+
+    // out[i] = sum_c A(I_i, J_c) zc[c] over the rows of I, in double
+    __device__ void rows_times(const double *zc, double *out) {
+        for (int i = team.rank(); i < q; i += Team::SIZE) {
+            const int32_t row = w.I[i];
+            const int64_t e0 = A.row_ptr[row], e1 = A.row_ptr[row + 1];
+            double acc = 0.0;
+            for (int64_t e = e0; e < e1; ++e) {
+                const int c = find_J(A.col_idx[e]);
+                if (c >= 0) acc = fma(A.val[e], zc[c], acc);
+            }
+            out[i] = acc;
+        }
+        team.sync();
+    }
+
+    // out[c] = sum_i A(I_i, J_c) v[i] over the columns of J, in double
+    __device__ void cols_times(const double *v, double *out) {
+        for (int c = team.rank(); c < p; c += Team::SIZE) {
+            const int32_t j = w.J[c];
+            double acc = 0.0;
+            for (int64_t e = A.col_ptr[j]; e < A.col_ptr[j + 1]; ++e)
+                acc = fma(A.cval[e], v[find_i32(w.I, q, A.row_idx[e])], acc);
+            out[c] = acc;
+        }
+        team.sync();
+    }
+
+    // rhs[0..p) <- (R^T R)^{-1} rhs[0..p) with R from the last solve
+    __device__ void normal_solve(T small) {
+        const int me = team.rank();
+        for (int i = 0; i < p; ++i) {  // R^T y = rhs (forward, column-oriented)
+            T d = w.B[(int64_t)i * q + i];
+            T yi = (fabs(d) <= small) ? T(0) : w.rhs[i] / d;
+            team.sync();
+            for (int c = i + 1 + me; c < p; c += Team::SIZE) w.rhs[c] -= w.B[(int64_t)c * q + i] * yi;
+            if (me == 0) w.rhs[i] = yi;
+            team.sync();
+        }
+        back_substitute_team(team, w.B, q, p, w.rhs, small);
+    }
+
+    // Refit: solve on the loaded pattern, then the residual.  Returns false on
+    // overflow.
+    __device__ bool refit() {
+        if (!solve(false)) return false;
+        residual();
+        return true;
+    }
+
+    // Adjoint of the frozen-pattern solve of column k (see rsai_backward):
+    //   x = m_k(J_k), r = B x - e_k(I_k), z = (B^T B)^{-1} g (one FP64
+    //   refinement step in FP32_REFINE), w = B z;  writes r, w over I_k and
+    //   alpha = -z + 2 gr x, x over J_k.
+    __device__ bool adjoint(const Frozen &F) {
+        const int me = team.rank();
+        if (!solve(false)) return false;
+        residual();
+        const int64_t mo = F.Mcolptr[k];
+        for (int c = me; c < p; c += Team::SIZE) w.z[c] = F.grad_M[F.Mcsc_to_csr[mo + c]];
+        team.sync();
+        const T small = small_last;
+        for (int c = me; c < p; c += Team::SIZE) w.rhs[c] = (T)w.z[c];
+        team.sync();
+        normal_solve(small);
+        if (P.precision == RSAI_FP32_REFINE) {
+            // one refinement step in double: z = z0 + (R^T R)^{-1} (g - B^T B z0);
+            // g stays in z, z0 goes to buf, B z0 to wv, B^T B z0 to buf2
+            double *z0 = reinterpret_cast<double *>(w.buf);
+            double *u = reinterpret_cast<double *>(w.buf2);
+            for (int c = me; c < p; c += Team::SIZE) z0[c] = (double)w.rhs[c];
+            team.sync();
+            rows_times(z0, w.wv);
+            cols_times(w.wv, u);
+            for (int c = me; c < p; c += Team::SIZE) w.rhs[c] = (T)(w.z[c] - u[c]);
+            team.sync();
+            normal_solve(small);
+            for (int c = me; c < p; c += Team::SIZE) w.z[c] = z0[c] + (double)w.rhs[c];
+            team.sync();
+        } else {
+            for (int c = me; c < p; c += Team::SIZE) w.z[c] = (double)w.rhs[c];
+            team.sync();
+        }
+        rows_times(w.z, w.wv);
+        const double gr = F.grad_rho2 ? F.grad_rho2[k] : 0.0;
+        const int64_t qo = F.qoff[k];
+        int pk = lower_bound_i32(w.I, q, k);
+        bool has_k = pk < q && w.I[pk] == k;
+        for (int i = me; i < q; i += Team::SIZE) {
+            const int si = (has_k || i < pk) ? i : i + 1;
+            F.poolI[qo + i] = w.I[i];
+            F.poolR[qo + i] = w.r[si];
+            F.poolW[qo + i] = w.wv[i];
+        }
+        for (int c = me; c < p; c += Team::SIZE) {
+            const double x = w.m[c];
+            F.alphaM[mo + c] = -w.z[c] + 2.0 * gr * x;
+            F.xM[mo + c] = x;
+        }
+        team.sync();
+        return true;
+    }
+
     __device__ int run() {
         const int me = team.rank();
         p = 1; q = 0; s = 0; nR = 0; l = 0; q0 = 0; p0 = 0; rank_flag = 0; rho = 0.0;

@@ -46,6 +46,7 @@ enum Counter {
 struct ColOut {
     int64_t *col_off;   // offset of the column in the result pool
     int32_t *col_len;   // nnz(m_k)
+    int32_t *col_q;     // |I_k| of the final pattern
     double *rho;        // ||r_k||
     int32_t *loops;
     int32_t *flags;     // RSAI_COL_*
@@ -54,6 +55,23 @@ struct ColOut {
     int64_t pool_cap;
     unsigned long long *pool_top;
     int32_t *err;       // first device error code (0 = none)
+};
+
+// Frozen-pattern passes (refit, backward): the pattern of M and the buffers
+// they read and write.  Unused (NULL) in the build.
+enum { MODE_BUILD = 0, MODE_REFIT = 1, MODE_BACKWARD = 2 };
+struct Frozen {
+    const int64_t *Mcolptr;      // CSC of M: column k is J_k
+    const int32_t *Mrows;
+    const int64_t *Mcsc_to_csr;  // CSR position of each CSC entry of M
+    double *Mval_csr;            // refit: new values of M (CSR order)
+    double *rho2;                // refit: ||r_k||^2
+    const double *grad_M;        // backward: dL/dM (CSR order of M)
+    const double *grad_rho2;     // backward: dL/d(rho_k^2) or NULL
+    const int64_t *qoff;         // backward: offset of column k's I_k in the pools
+    int32_t *poolI;              // backward: I_k
+    double *poolR, *poolW;       // backward: r_k(I_k), (B_k z_k)(I_k)
+    double *alphaM, *xM;         // backward: -z + 2 g x and x, per entry of M (CSC order)
 };
 
 // Queue of columns for one bin.

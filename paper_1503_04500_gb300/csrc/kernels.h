@@ -33,12 +33,17 @@ __global__ void k_sort_rows(const int64_t *Mrowptr, const int32_t *tcols, const 
 
 template <typename T> size_t work_bytes(const Caps &c);
 
-cudaError_t launch_bin_warp(bool fp32, int grid, int warps, const DevA &A, const DevParams &P, const Caps &cap,
-                            const ColQueue &Q, const ColOut &O, unsigned long long *gctr, bool last,
-                            cudaStream_t st);
-cudaError_t launch_bin_block(bool fp32, int grid, const DevA &A, const DevParams &P, const Caps &cap,
-                             const ColQueue &Q, const ColOut &O, unsigned long long *gctr, bool last, char *gwork,
-                             size_t gstride, int bin, cudaStream_t st);
+cudaError_t launch_bin_warp(int mode, bool fp32, int grid, int warps, const DevA &A, const DevParams &P,
+                            const Caps &cap, const ColQueue &Q, const ColOut &O, const Frozen &F,
+                            unsigned long long *gctr, bool last, cudaStream_t st);
+cudaError_t launch_bin_block(int mode, bool fp32, int grid, const DevA &A, const DevParams &P, const Caps &cap,
+                             const ColQueue &Q, const ColOut &O, const Frozen &F, unsigned long long *gctr,
+                             bool last, char *gwork, size_t gstride, int bin, cudaStream_t st);
+cudaError_t launch_adjoint_gather(int64_t n, int64_t nnzM, const int64_t *row_ptr, const int32_t *col_idx,
+                                  const int64_t *Mrowptr, const int32_t *Mcols, const int64_t *Mcsc_to_csr,
+                                  int64_t *Mcsr_to_csc, const int64_t *qoff, const int32_t *poolI,
+                                  const double *poolR, const double *poolW, const double *alphaM,
+                                  const double *xM, double *grad, cudaStream_t st);
 int occupancy_bin_warp(bool fp32, int warps, const Caps &cap);
 int occupancy_bin_block(bool fp32, const Caps &cap, bool global_work);
 

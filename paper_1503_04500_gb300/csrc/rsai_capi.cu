@@ -34,7 +34,7 @@ struct rsai_handle {
     int64_t ovf_cap = 0;
     // per column
     int64_t *col_off = nullptr;
-    int32_t *col_len = nullptr, *loops = nullptr, *flags = nullptr;
+    int32_t *col_len = nullptr, *col_q = nullptr, *loops = nullptr, *flags = nullptr;
     double *rho = nullptr;
     // pool
     int32_t *pool_rows = nullptr;
@@ -54,6 +54,13 @@ struct rsai_handle {
     // bins
     Caps capW{}, capC{}, capG{};
     int grid_w = 0, grid_c = 0;
+    // refit / backward scratch (allocated on first use)
+    double *fval = nullptr, *fcval = nullptr;
+    int64_t *qoff = nullptr, *Mcsr_to_csc = nullptr;
+    int32_t *poolI = nullptr;
+    double *poolR = nullptr, *poolW = nullptr, *alphaM = nullptr, *xM = nullptr;
+    int64_t pool_q_cap = 0, adj_m_cap = 0;
+    unsigned long long *fctr = nullptr;  // work counters of refit / backward passes
     // graph
     cudaGraphExec_t graph = nullptr;
     cudaStream_t graph_stream = nullptr;
@@ -120,6 +127,30 @@ cudaError_t scan_counts(rsai_handle *h, const int32_t *in, int64_t *out, cudaStr
     return cudaGetLastError();
 }
 
+// The three bins over all columns (mode: build, refit or backward); queue
+// counters are reset first.  `ev` (optional) brackets the bins (ev[1..4]).
+cudaError_t enqueue_bins(rsai_handle *h, int mode, const DevA &A, const Frozen &F, unsigned long long *gctr,
+                         cudaStream_t st, cudaEvent_t *ev = nullptr) {
+    const int64_t n = h->n;
+    cudaMemsetAsync(h->qnext, 0, sizeof(uint32_t) * 8, st);
+    const DevParams P = dev_params(h);
+    const bool fp32 = h->params.precision == RSAI_FP32_REFINE;
+    ColOut O{h->col_off, h->col_len, h->col_q, h->rho, h->loops, h->flags, h->pool_rows, h->pool_vals,
+             h->pool_cap, h->pool_top, h->err};
+    ColQueue QW{nullptr, nullptr, n, h->qnext + 0, h->ovf1, h->qnext + 3, h->ovf_cap};
+    ColQueue QC{h->ovf1, h->qnext + 3, n, h->qnext + 1, h->ovf2, h->qnext + 4, h->ovf_cap};
+    ColQueue QG{h->ovf2, h->qnext + 4, n, h->qnext + 2, nullptr, nullptr, 0};
+    if (ev) cudaEventRecord(ev[1], st);
+    cudaError_t e = launch_bin_warp(mode, fp32, h->grid_w, kWarpsPerCta, A, P, h->capW, QW, O, F, gctr, false, st);
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[2], st);
+    e = launch_bin_block(mode, fp32, h->grid_c, A, P, h->capC, QC, O, F, gctr, false, nullptr, 0, 1, st);
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[3], st);
+    e = launch_bin_block(mode, fp32, h->grid_g, A, P, h->capG, QG, O, F, gctr, true, h->gwork, h->gstride, 2, st);
+    return e;
+}
+
 // The build sequence: no allocation, no host synchronisation (capturable).
 // `ev` (optional, RSAI_PHASE_COUNT + 1 events) are recorded between phases.
 cudaError_t enqueue_build(rsai_handle *h, cudaStream_t st, cudaEvent_t *ev = nullptr) {
@@ -134,23 +165,7 @@ cudaError_t enqueue_build(rsai_handle *h, cudaStream_t st, cudaEvent_t *ev = nul
     k_norm1<<<blocks(n, 256), 256, 0, st>>>(h->col_ptr, h->cval, n, dword(h, kNorm1));
     k_tau_fixed<<<1, 1, 0, st>>>(dword(h, kNorm1), h->params.tol, dword(h, kTau));
 
-    const DevA A = dev_a(h);
-    const DevParams P = dev_params(h);
-    const bool fp32 = h->params.precision == RSAI_FP32_REFINE;
-    unsigned long long *gctr = h->dscal + kCtr;
-    ColOut O{h->col_off, h->col_len, h->rho, h->loops, h->flags, h->pool_rows, h->pool_vals,
-             h->pool_cap, h->pool_top, h->err};
-    ColQueue QW{nullptr, nullptr, n, h->qnext + 0, h->ovf1, h->qnext + 3, h->ovf_cap};
-    ColQueue QC{h->ovf1, h->qnext + 3, n, h->qnext + 1, h->ovf2, h->qnext + 4, h->ovf_cap};
-    ColQueue QG{h->ovf2, h->qnext + 4, n, h->qnext + 2, nullptr, nullptr, 0};
-    if (ev) cudaEventRecord(ev[1], st);
-    cudaError_t e = launch_bin_warp(fp32, h->grid_w, kWarpsPerCta, A, P, h->capW, QW, O, gctr, false, st);
-    if (e != cudaSuccess) return e;
-    if (ev) cudaEventRecord(ev[2], st);
-    e = launch_bin_block(fp32, h->grid_c, A, P, h->capC, QC, O, gctr, false, nullptr, 0, 1, st);
-    if (e != cudaSuccess) return e;
-    if (ev) cudaEventRecord(ev[3], st);
-    e = launch_bin_block(fp32, h->grid_g, A, P, h->capG, QG, O, gctr, true, h->gwork, h->gstride, 2, st);
+    cudaError_t e = enqueue_bins(h, MODE_BUILD, dev_a(h), Frozen{}, h->dscal + kCtr, st, ev);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[4], st);
     k_column_stats<<<kStatBlocks, 256, 0, st>>>(h->rho, h->flags, h->col_len, n, h->params.eps,
@@ -342,6 +357,7 @@ rsai_status rsai_build(const rsai_csr *A, const rsai_csc *Acsc, const rsai_param
     TRY(dalloc(h, &h->ovf2, n, st));
     TRY(dalloc(h, &h->col_off, n, st));
     TRY(dalloc(h, &h->col_len, n, st));
+    TRY(dalloc(h, &h->col_q, n, st));
     TRY(dalloc(h, &h->loops, n, st));
     TRY(dalloc(h, &h->flags, n, st));
     TRY(dalloc(h, &h->rho, n, st));
@@ -525,15 +541,122 @@ rsai_status rsai_bicgstab(const rsai_csr *A, rsai_handle *M, const double *b, do
     return (rsai_status)rc;
 }
 
+}  // extern "C"
+
+namespace {
+
+// values of A for a frozen-pattern pass: CSR copy + CSC through the map
+int frozen_values(rsai_handle *h, const double *A_val, cudaStream_t st, DevA *out) {
+    if (!h->fval) {
+        int rc = dalloc(h, &h->fval, h->nnz, st);
+        if (rc == RSAI_OK) rc = dalloc(h, &h->fcval, h->nnz, st);
+        if (rc == RSAI_OK) rc = dalloc(h, &h->fctr, CTR_COUNT + 3, st);
+        if (rc != RSAI_OK) return rc;
+    }
+    cudaMemsetAsync(h->fctr, 0, sizeof(unsigned long long) * (CTR_COUNT + 3), st);
+    if (cudaMemcpyAsync(h->fval, A_val, sizeof(double) * h->nnz, cudaMemcpyDefault, st) != cudaSuccess)
+        return RSAI_ERR_CUDA;
+    k_csc_from_csr<<<blocks(h->nnz, 256), 256, 0, st>>>(h->fval, h->csc_to_csr, h->fcval, h->nnz);
+    *out = DevA{h->n, h->row_ptr, h->col_idx, h->fval, h->col_ptr, h->row_idx, h->fcval};
+    return cuda_status(cudaGetLastError());
+}
+
+int64_t nnz_of_M(rsai_handle *h, cudaStream_t st) {
+    int64_t nnzM = -1;
+    if (cudaMemcpyAsync(&nnzM, h->Mrowptr + h->n, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return -1;
+    return nnzM;
+}
+
+int finish_frozen(rsai_handle *h, cudaStream_t st) {
+    int32_t herr = 0;
+    cudaMemcpyAsync(&herr, h->err, sizeof(herr), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return RSAI_ERR_CUDA;
+    return herr;
+}
+
+}  // namespace
+
+extern "C" {
+
 rsai_status rsai_refit(rsai_handle *h, const double *A_val, double *M_val, double *rho2, void *stream) {
-    (void)h; (void)A_val; (void)M_val; (void)rho2; (void)stream;
-    return RSAI_ERR_INVALID_ARG;
+    if (!h || !A_val) return RSAI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nnzM = nnz_of_M(h, st);
+    if (nnzM < 0) return RSAI_ERR_CUDA;
+    DevA A;
+    int rc = frozen_values(h, A_val, st, &A);
+    if (rc != RSAI_OK) return (rsai_status)rc;
+    double *mv = M_val, *r2 = rho2;
+    double *tmp = nullptr;
+    if (!mv || !r2) {  // outputs the caller skipped go to a temporary
+        if (cudaMallocAsync((void **)&tmp, sizeof(double) * (size_t)(nnzM + h->n + 1), st) != cudaSuccess)
+            return RSAI_ERR_OOM;
+        if (!mv) mv = tmp;
+        if (!r2) r2 = tmp + nnzM;
+    }
+    Frozen F{};
+    F.Mcolptr = h->Mcolptr;
+    F.Mrows = h->Mrows;
+    F.Mcsc_to_csr = h->Mcsc_to_csr;
+    F.Mval_csr = mv;
+    F.rho2 = r2;
+    cudaMemsetAsync(h->err, 0, sizeof(int32_t), st);
+    cudaError_t e = enqueue_bins(h, MODE_REFIT, A, F, h->fctr, st);
+    if (tmp) cudaFreeAsync(tmp, st);
+    if (e != cudaSuccess) return RSAI_ERR_CUDA;
+    return (rsai_status)finish_frozen(h, st);
 }
 
 rsai_status rsai_backward(rsai_handle *h, const double *A_val, const double *grad_M, const double *grad_rho2,
                           double *grad_A, void *stream) {
-    (void)h; (void)A_val; (void)grad_M; (void)grad_rho2; (void)grad_A; (void)stream;
-    return RSAI_ERR_INVALID_ARG;
+    if (!h || !A_val || !grad_M || !grad_A) return RSAI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nnzM = nnz_of_M(h, st);
+    if (nnzM < 0) return RSAI_ERR_CUDA;
+    DevA A;
+    int rc = frozen_values(h, A_val, st, &A);
+    if (rc != RSAI_OK) return (rsai_status)rc;
+    // offsets of the I_k (|I_k| recorded by the build)
+    if (!h->qoff && (rc = dalloc(h, &h->qoff, h->n + 1, st)) != RSAI_OK) return (rsai_status)rc;
+    if (scan_counts(h, h->col_q, h->qoff, st) != cudaSuccess) return RSAI_ERR_CUDA;
+    int64_t qtot = 0;
+    cudaMemcpyAsync(&qtot, h->qoff + h->n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return RSAI_ERR_CUDA;
+    if (qtot > h->pool_q_cap) {
+        int rc2 = dalloc(h, &h->poolI, qtot, st);
+        if (rc2 == RSAI_OK) rc2 = dalloc(h, &h->poolR, qtot, st);
+        if (rc2 == RSAI_OK) rc2 = dalloc(h, &h->poolW, qtot, st);
+        if (rc2 != RSAI_OK) return (rsai_status)rc2;
+        h->pool_q_cap = qtot;
+    }
+    if (nnzM > h->adj_m_cap) {
+        int rc2 = dalloc(h, &h->alphaM, nnzM, st);
+        if (rc2 == RSAI_OK) rc2 = dalloc(h, &h->xM, nnzM, st);
+        if (rc2 == RSAI_OK) rc2 = dalloc(h, &h->Mcsr_to_csc, nnzM, st);
+        if (rc2 != RSAI_OK) return (rsai_status)rc2;
+        h->adj_m_cap = nnzM;
+    }
+    Frozen F{};
+    F.Mcolptr = h->Mcolptr;
+    F.Mrows = h->Mrows;
+    F.Mcsc_to_csr = h->Mcsc_to_csr;
+    F.grad_M = grad_M;
+    F.grad_rho2 = grad_rho2;
+    F.qoff = h->qoff;
+    F.poolI = h->poolI;
+    F.poolR = h->poolR;
+    F.poolW = h->poolW;
+    F.alphaM = h->alphaM;
+    F.xM = h->xM;
+    cudaMemsetAsync(h->err, 0, sizeof(int32_t), st);
+    if (enqueue_bins(h, MODE_BACKWARD, A, F, h->fctr, st) != cudaSuccess) return RSAI_ERR_CUDA;
+    if (launch_adjoint_gather(h->n, nnzM, h->row_ptr, h->col_idx, h->Mrowptr, h->Mcols, h->Mcsc_to_csr,
+                              h->Mcsr_to_csc, h->qoff, h->poolI, h->poolR, h->poolW, h->alphaM, h->xM, grad_A,
+                              st) != cudaSuccess)
+        return RSAI_ERR_CUDA;
+    return (rsai_status)finish_frozen(h, st);
 }
 
 rsai_status rsai_build_phase_times(rsai_handle *h, void *stream, double *ms) {

@@ -278,6 +278,7 @@ class Handle:
         return y
 
     def refit(self, A_val, stream=None):
+        """rsai_refit: (values of M in its CSR order, rho_k^2) on the frozen pattern."""
         import torch
 
         nnz = self.stats(stream)["nnz_M"]
@@ -287,6 +288,7 @@ class Handle:
         return mv[:nnz], rho2
 
     def backward(self, A_val, grad_M, grad_rho2=None, stream=None):
+        """rsai_backward: dL/d(values of A) for dL/dM (CSR order of M) and dL/d(rho_k^2)."""
         import torch
 
         g = torch.empty_like(A_val)

@@ -1,0 +1,105 @@
+"""GPU refit and adjoint (rsai_refit, rsai_backward) against the oracle, closed forms and differences."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1503_04500_gb300 import inputs as gen
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+rsai = pytest.importorskip("paper_1503_04500_gb300.rsai")
+from paper_1503_04500_gb300.autograd import frozen_rsai  # noqa: E402
+
+KW = dict(c=3, l_max=10, eps=0.3, tol=1e-3, drop="fixed")
+
+
+def _setup(precision, N=16):
+    P = gen.parametric2d(N, (30.0, 10.0))
+    A = P.base
+    dA = rsai.DeviceMatrix.from_host(A)
+    h = rsai.build(dA, precision=precision, **KW)
+    rp, ci, va = (t.cpu().numpy() for t in h.M())
+    # oracle pattern from the GPU's M (CSC of M)
+    rows = np.repeat(np.arange(A.n), np.diff(rp))
+    order = np.lexsort((rows, ci))
+    colptr = np.zeros(A.n + 1, np.int64)
+    np.add.at(colptr, ci.astype(np.int64) + 1, 1)
+    colptr = np.cumsum(colptr)
+    Mrows = rows[order].astype(np.int32)
+    csc_pos = order  # CSR position of each CSC entry
+    return P, A, dA, h, (rp, ci, va), colptr, Mrows, csc_pos
+
+
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-11), ("fp32_refine", 1e-6)])
+def test_refit_matches_oracle(precision, rtol):
+    P, A, dA, h, (rp, ci, va), colptr, Mrows, csc_pos = _setup(precision)
+    vals2 = A.val * (1.0 + 0.05 * np.cos(np.arange(A.nnz)))
+    mv, rho2 = h.refit(torch.as_tensor(vals2, device="cuda"))
+    ov, orho2 = oracle.refit(A.with_values(vals2), colptr, Mrows)
+    got = mv.cpu().numpy()[csc_pos]
+    np.testing.assert_allclose(got, ov, rtol=rtol, atol=rtol * np.abs(ov).max())
+    np.testing.assert_allclose(rho2.cpu().numpy(), orho2, rtol=10 * rtol)
+    # refit at the build's own values reproduces M
+    mv0, _ = h.refit(dA.val)
+    np.testing.assert_allclose(mv0.cpu().numpy(), va, rtol=rtol, atol=rtol * np.abs(va).max())
+
+
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-9), ("fp32_refine", 1e-5)])
+def test_backward_matches_oracle(precision, rtol):
+    P, A, dA, h, (rp, ci, va), colptr, Mrows, csc_pos = _setup(precision)
+    rng = np.random.default_rng(11)
+    gM_csr = rng.standard_normal(len(va))
+    gr = rng.standard_normal(A.n)
+    g = h.backward(dA.val, torch.as_tensor(gM_csr, device="cuda"), torch.as_tensor(gr, device="cuda"))
+    go = oracle.backward(A, colptr, Mrows, gM_csr[csc_pos], gr)
+    np.testing.assert_allclose(g.cpu().numpy(), go, rtol=rtol, atol=rtol * np.abs(go).max())
+
+
+def test_backward_frobenius_closed_form():
+    """L = ||AM-I||_F^2 on the frozen pattern: dL/dA = 2 (AM - I) M^T on struct(A)."""
+    P, A, dA, h, (rp, ci, va), colptr, Mrows, csc_pos = _setup("fp64")
+    g = h.backward(dA.val, torch.zeros(len(va), dtype=torch.float64, device="cuda"),
+                   torch.ones(A.n, dtype=torch.float64, device="cuda")).cpu().numpy()
+    D = A.to_dense()
+    Md = np.zeros((A.n, A.n))
+    Md[np.repeat(np.arange(A.n), np.diff(rp)), ci] = va
+    full = 2.0 * (D @ Md - np.eye(A.n)) @ Md.T
+    expect = full[np.repeat(np.arange(A.n), np.diff(A.row_ptr)), A.col_idx]
+    np.testing.assert_allclose(g, expect, rtol=1e-9, atol=1e-12 * np.abs(expect).max())
+
+
+def test_backward_deterministic():
+    P, A, dA, h, (rp, ci, va), *_ = _setup("fp64")
+    gM = torch.linspace(-1, 1, len(va), dtype=torch.float64, device="cuda")
+    gr = torch.linspace(0, 1, A.n, dtype=torch.float64, device="cuda")
+    a = h.backward(dA.val, gM, gr)
+    b = h.backward(dA.val, gM, gr)
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-6), ("fp32_refine", 1e-4)])
+def test_theta_gradient_central_differences(precision, rtol):
+    """A(theta) = L + theta1 Cx + theta2 Cy; loss = sum_k rho_k^2 + <w, M>: autograd vs central FD (h = 1e-6)."""
+    P, A, dA, h, (rp, ci, va), *_ = _setup(precision)
+    L = torch.as_tensor(P.L, device="cuda")
+    Cx = torch.as_tensor(P.C[0], device="cuda")
+    Cy = torch.as_tensor(P.C[1], device="cuda")
+    wgt = torch.linspace(-1, 1, len(va), dtype=torch.float64, device="cuda")
+
+    def loss_of(theta):
+        A_val = L + theta[0] * Cx + theta[1] * Cy
+        M_val, rho2 = frozen_rsai(A_val, h)
+        return rho2.sum() + (wgt * M_val).sum()
+
+    theta = torch.tensor([30.0, 10.0], dtype=torch.float64, device="cuda", requires_grad=True)
+    loss = loss_of(theta)
+    loss.backward()
+    g = theta.grad.cpu().numpy()
+    fd = []
+    for i in range(2):
+        e = torch.zeros(2, dtype=torch.float64, device="cuda")
+        e[i] = 1e-6 * 30.0
+        with torch.no_grad():
+            fd.append(float((loss_of(theta + e) - loss_of(theta - e)) / (2 * e[i])))
+    np.testing.assert_allclose(g, fd, rtol=rtol)
