@@ -268,6 +268,30 @@ def main():
     dev_ms64 = max_over_ranks(sum(ms64)) / k64
     s64 = h64.stats()
 
+    # adjoint on the frozen pattern (loss ||AM - I||_F^2: dL/dM = 0, dL/drho_k^2 = 1)
+    def bwd_ms(handle, steps):
+        nnz = handle.stats()["nnz_M"]
+        gM = torch.zeros(nnz, dtype=torch.float64, device="cuda")
+        gr = torch.ones(A.n, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            handle.backward(dA.val, gM, gr)
+        st = torch.cuda.current_stream()
+        out = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            handle.backward(dA.val, gM, gr)
+            e1.record(st)
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return max_over_ranks(statistics.median(out))
+
+    kb = max(3, args.steps // 10)
+    bwd32 = bwd_ms(h32, kb)
+    bwd64 = bwd_ms(h64, kb)
+
     # roofline of the dominant kernel (the warp bin): live per-phase CUDA events
     phases32, phases64 = [], []
     for _ in range(5):
@@ -354,7 +378,8 @@ def main():
                  "nnz_M": s64["nnz_M"], "roofline": roof64, "phases_ms": ph64},
         "frob_rel_diff_fp32r_vs_fp64": abs(s32["frob"] - s64["frob"]) / s64["frob"],
         "speedup_fp32r_vs_fp64": dev_ms64 / dev_ms,
-        "bwd_fwd_ratio": None,
+        "bwd_fwd_ratio": bwd32 / dev_ms,
+        "bwd_ms": bwd32, "bwd_fwd_ratio_fp64": bwd64 / dev_ms64,
         "roofline": roof32, "phases_ms": ph32,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": KERNELS_PER_BUILD * args.steps,
