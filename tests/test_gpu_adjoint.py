@@ -80,26 +80,30 @@ def test_backward_deterministic():
 
 @pytest.mark.parametrize("precision,rtol", [("fp64", 1e-6), ("fp32_refine", 1e-4)])
 def test_theta_gradient_central_differences(precision, rtol):
-    """A(theta) = L + theta1 Cx + theta2 Cy; loss = sum_k rho_k^2 + <w, M>: autograd vs central FD (h = 1e-6)."""
-    P, A, dA, h, (rp, ci, va), *_ = _setup(precision)
+    """A(theta) = L + theta1 Cx + theta2 Cy; loss = sum_k rho_k^2 + <w, M>: the autograd gradient
+    (FP64 or FP32+refine adjoint) against central differences (step 1e-6 relative) of the FP64
+    frozen-pattern loss, evaluated by the oracle's refit on the same pattern."""
+    P, A, dA, h, (rp, ci, va), colptr, Mrows, csc_pos = _setup(precision)
     L = torch.as_tensor(P.L, device="cuda")
     Cx = torch.as_tensor(P.C[0], device="cuda")
     Cy = torch.as_tensor(P.C[1], device="cuda")
     wgt = torch.linspace(-1, 1, len(va), dtype=torch.float64, device="cuda")
-
-    def loss_of(theta):
-        A_val = L + theta[0] * Cx + theta[1] * Cy
-        M_val, rho2 = frozen_rsai(A_val, h)
-        return rho2.sum() + (wgt * M_val).sum()
-
     theta = torch.tensor([30.0, 10.0], dtype=torch.float64, device="cuda", requires_grad=True)
-    loss = loss_of(theta)
-    loss.backward()
+    M_val, rho2 = frozen_rsai(L + theta[0] * Cx + theta[1] * Cy, h)
+    (rho2.sum() + (wgt * M_val).sum()).backward()
     g = theta.grad.cpu().numpy()
+    w_csc = wgt.cpu().numpy()[csc_pos]
+
+    def loss_fd(th):
+        vals, r2 = oracle.refit(A.with_values(P.values(th)), colptr, Mrows)
+        return float(r2.sum() + w_csc @ vals)
+
     fd = []
     for i in range(2):
-        e = torch.zeros(2, dtype=torch.float64, device="cuda")
-        e[i] = 1e-6 * 30.0
-        with torch.no_grad():
-            fd.append(float((loss_of(theta + e) - loss_of(theta - e)) / (2 * e[i])))
-    np.testing.assert_allclose(g, fd, rtol=rtol)
+        step = 1e-6 * 30.0
+        tp = [30.0, 10.0]
+        tm = [30.0, 10.0]
+        tp[i] += step
+        tm[i] -= step
+        fd.append((loss_fd(tp) - loss_fd(tm)) / (2 * step))
+    np.testing.assert_allclose(g, fd, rtol=rtol, atol=rtol * np.abs(fd).max())
