@@ -163,6 +163,27 @@ rsai_status rsai_build(const rsai_csr *A, const rsai_csc *Acsc, const rsai_param
                        void *stream, rsai_handle **out);
 
 /*
+ * rsai_build_batch -- build M for `count` independent matrices in one
+ * sequence of launches (Eq. 2.2 over all their columns at once).  The members
+ * are placed side by side as one block-diagonal matrix: a column's pattern
+ * never leaves its block (I_k, the dominant rows and the new columns all stay
+ * in it), and ||A||_1 of the drop rule (Eq. 4.3) is taken per member, so every
+ * block of the result equals the member's own build.
+ *   As[b], Acscs[b] : member b in CSR and CSC (host or device arrays), b < count.
+ * The handle's M is block diagonal (n = sum of the members' n); read it with
+ * rsai_get_M and split it by the members' sizes; per-member statistics come
+ * from rsai_get_block_stats.  rsai_rebuild, rsai_refit, rsai_backward and
+ * rsai_apply work on the whole batch.  Errors as rsai_build.
+ */
+rsai_status rsai_build_batch(const rsai_csr *As, const rsai_csc *Acscs, int32_t count, const rsai_params *params,
+                             void *stream, rsai_handle **out);
+
+/* Per-member ||A_b M_b - I||_F, n_c and nnz(M_b) of a batch handle (one entry
+ * for a single-matrix handle); host arrays of `count` entries, any may be
+ * NULL.  Synchronises the stream. */
+rsai_status rsai_get_block_stats(rsai_handle *h, void *stream, double *frob, int64_t *n_c, int64_t *nnz_M);
+
+/*
  * rsai_rebuild -- run the build again on the handle's own copy of A after
  * new values were written with rsai_set_values (same structure), reusing every
  * buffer: no allocation, no host synchronisation; the launch sequence is

@@ -61,16 +61,77 @@ __global__ void k_csc_from_csr(const double *csr_val, const int64_t *csc_to_csr,
     if (e < nnz) cval[e] = csr_val[csc_to_csr[e]];
 }
 
-// ||A||_1 = max_j sum_i |a_ij| (Eq. 4.3); nonnegative doubles order like their bits
-__global__ void k_norm1(const int64_t *col_ptr, const double *cval, int64_t n, double *out) {
+// ||A||_1 = max_j sum_i |a_ij| (Eq. 4.3), per block of columns; nonnegative
+// doubles order like their bits
+__global__ void k_norm1(const int64_t *col_ptr, const double *cval, int64_t n, const int32_t *col_block,
+                        double *out) {
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
     double s = 0.0;
-    if (j < n)
-        for (int64_t e = col_ptr[j]; e < col_ptr[j + 1]; ++e) s += fabs(cval[e]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
-    if ((threadIdx.x & 31) == 0)
-        atomicMax((unsigned long long *)out, (unsigned long long)__double_as_longlong(s));
+    for (int64_t e = col_ptr[j]; e < col_ptr[j + 1]; ++e) s += fabs(cval[e]);
+    const int b = col_block ? col_block[j] : 0;
+    atomicMax((unsigned long long *)&out[b], (unsigned long long)__double_as_longlong(s));
+}
+
+// block of every column from the block start offsets
+__global__ void k_col_block(const int64_t *cstart, int32_t nblocks, int64_t n, int32_t *col_block) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int lo = 0, hi = nblocks;  // last b with cstart[b] <= j
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (cstart[mid] <= j) lo = mid; else hi = mid;
+    }
+    col_block[j] = lo;
+}
+
+// pointers and indices of members copied side by side become one
+// block-diagonal matrix: pointers += nnz offset, indices += column offset
+__global__ void k_shift_ptr(int64_t *ptr, int64_t n, const int32_t *col_block, const int64_t *estart,
+                            int64_t nnz_total) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) ptr[i] += estart[col_block[i]];
+    if (i == n) ptr[n] = nnz_total;
+}
+__global__ void k_shift_idx(const int64_t *ptr, int32_t *idx, int64_t n, const int32_t *col_block,
+                            const int64_t *cstart) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t off = (int32_t)cstart[col_block[i]];
+    for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) idx[e] += off;
+}
+
+// per-block ||AM - I||_F^2, n_c and nnz(M) in a fixed order (one CTA per block)
+__global__ void k_block_stats(const int64_t *cstart, const double *rho, const int32_t *flags, const int32_t *len,
+                              double eps, double *frob2, long long *nc, long long *nnz) {
+    __shared__ double sh[256];
+    __shared__ long long s1[256], s2[256];
+    const int b = blockIdx.x;
+    double a = 0.0;
+    long long c = 0, z = 0;
+    for (int64_t k = cstart[b] + threadIdx.x; k < cstart[b + 1]; k += 256) {
+        const bool failed = flags[k] & RSAI_COL_FAILED;
+        if (!failed) a = fma(rho[k], rho[k], a);
+        c += (failed || abskey(rho[k]) > abskey(eps)) ? 1 : 0;
+        z += len[k];
+    }
+    sh[threadIdx.x] = a;
+    s1[threadIdx.x] = c;
+    s2[threadIdx.x] = z;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sh[threadIdx.x] += sh[threadIdx.x + o];
+            s1[threadIdx.x] += s1[threadIdx.x + o];
+            s2[threadIdx.x] += s2[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        frob2[b] = sh[0];
+        nc[b] = s1[0];
+        nnz[b] = s2[0];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -313,8 +374,11 @@ __global__ void k_column_stats_final(const double *partial, double *frob2) {
     if (threadIdx.x == 0) *frob2 = sh[0];
 }
 
-// tol / ||A||_1, the threshold of the fixed drop rule, once per build
-__global__ void k_tau_fixed(const double *norm1, double tol, double *tau) { *tau = tol / *norm1; }
+// tol / ||A||_1, the threshold of the fixed drop rule, once per build and block
+__global__ void k_tau_fixed(const double *norm1, double tol, double *tau, int32_t nblocks) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nblocks) tau[b] = tol / norm1[b];
+}
 
 // ---------------------------------------------------------------------------
 // exclusive scan of int32 counts into int64 offsets (three passes)

@@ -138,34 +138,37 @@ __device__ void back_substitute_team(const Team &team, const T *B, int q, int p,
 // Householder QR of B (q x p, column-major, ld q) applied to rhs, then back
 // substitution into rhs[0..p).  Keeps the reflectors (v_j below the diagonal
 // of B, heads in vhead, v^T v in vtv) for the refinement solve.  Returns the
-// rank flag.  Team-generic (rows strided over the team, one team reduction per
-// trailing column); not inlined.
+// rank flag.  Team-generic: the norm of the pivot column is one team
+// reduction; the trailing columns (and rhs) are dealt out to the team's warps,
+// each warp forming its column's dot product with the reflector (lanes over
+// rows, one warp reduction) and applying the update itself, so a step costs
+// one team synchronisation instead of one per column.  Not inlined.
 template <class Team, typename T>
 __device__ __noinline__ int qr_solve_team(Team team, T *B, int q, int p, T *rhs, T *vhead, T *vtvs, T small) {
     const int me = team.rank();
+    const int lane = me & 31, wid = me >> 5;
+    constexpr int NW = (Team::SIZE + 31) / 32;
     int rank_flag = 0;
     for (int j = 0; j < p; ++j) {
         T *col = B + (int64_t)j * q;
         T part = 0;
-        for (int i = me; i < q; i += Team::SIZE)
-            if (i >= j) part += col[i] * col[i];
-        T sigma = team.sum(part);
-        T x0 = col[j];
-        T nrm = sqrt(sigma);
-        T alpha = (x0 >= T(0)) ? -nrm : nrm;
-        T v0 = x0 - alpha;
-        T vtv = sigma - x0 * x0 + v0 * v0;
+        for (int i = j + me; i < q; i += Team::SIZE) part += col[i] * col[i];
+        const T sigma = team.sum(part);
+        const T x0 = col[j];
+        const T nrm = sqrt(sigma);
+        const T alpha = (x0 >= T(0)) ? -nrm : nrm;
+        const T v0 = x0 - alpha;
+        const T vtv = sigma - x0 * x0 + v0 * v0;
         if (vtv > T(0)) {
             const T two_over = T(2) / vtv;
-            for (int c = j + 1; c <= p; ++c) {
+            for (int c = j + 1 + wid; c <= p; c += NW) {
                 T *t = (c < p) ? B + (int64_t)c * q : rhs;
                 T d = 0;
-                for (int i = me; i < q; i += Team::SIZE)
-                    if (i >= j) d += ((i == j) ? v0 : col[i]) * t[i];
-                T sdot = team.sum(d);
-                T f = sdot * two_over;
-                for (int i = me; i < q; i += Team::SIZE)
-                    if (i >= j) t[i] -= f * ((i == j) ? v0 : col[i]);
+                for (int i = j + lane; i < q; i += 32) d += ((i == j) ? v0 : col[i]) * t[i];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                const T f = d * two_over;
+                for (int i = j + lane; i < q; i += 32) t[i] -= f * ((i == j) ? v0 : col[i]);
             }
         }
         team.sync();
@@ -464,7 +467,8 @@ template <class Team, typename T> struct Column {
     __device__ bool drop() {
         if (P.drop_mode == RSAI_DROP_NONE) return false;
         const int me = team.rank();
-        const double tau = (P.drop_mode == RSAI_DROP_ADAPTIVE) ? P.eps / ((double)p * *P.norm1) : *P.tau_fixed;
+        const int blk = P.col_block ? P.col_block[k] : 0;
+        const double tau = (P.drop_mode == RSAI_DROP_ADAPTIVE) ? P.eps / ((double)p * P.norm1[blk]) : P.tau_fixed[blk];
         const long long tk = abskey(tau);
         int nkeep = 0;
         long long ba = -1;

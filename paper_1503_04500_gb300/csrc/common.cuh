@@ -31,8 +31,9 @@ struct DevA {
 struct DevParams {
     int c, l_max, drop_mode, precision;
     double eps, tol, tie_band;
-    const double *norm1;      // ||A||_1 on the device (computed by a kernel)
-    const double *tau_fixed;  // tol / ||A||_1 (computed once per build)
+    const double *norm1;       // ||A||_1 per block (one block unless a batch)
+    const double *tau_fixed;   // tol / ||A||_1 per block
+    const int32_t *col_block;  // block of each column (NULL: one block)
 };
 
 // Work counters of one team, summed into the global statistics at the end.

@@ -14,11 +14,19 @@ __global__ void k_check_ptr(const int64_t *ptr, int64_t n, int64_t nnz, int32_t 
 __global__ void k_check_idx(const int64_t *ptr, const int32_t *idx, int64_t n, int32_t *err, int empty_is_error);
 __global__ void k_csc_map(DevA A, int64_t *csc_to_csr, int32_t *err);
 __global__ void k_csc_from_csr(const double *csr_val, const int64_t *csc_to_csr, double *cval, int64_t nnz);
-__global__ void k_norm1(const int64_t *col_ptr, const double *cval, int64_t n, double *out);
+__global__ void k_norm1(const int64_t *col_ptr, const double *cval, int64_t n, const int32_t *col_block,
+                        double *out);
+__global__ void k_col_block(const int64_t *cstart, int32_t nblocks, int64_t n, int32_t *col_block);
+__global__ void k_shift_ptr(int64_t *ptr, int64_t n, const int32_t *col_block, const int64_t *estart,
+                            int64_t nnz_total);
+__global__ void k_shift_idx(const int64_t *ptr, int32_t *idx, int64_t n, const int32_t *col_block,
+                            const int64_t *cstart);
+__global__ void k_block_stats(const int64_t *cstart, const double *rho, const int32_t *flags, const int32_t *len,
+                              double eps, double *frob2, long long *nc, long long *nnz);
 __global__ void k_column_stats(const double *rho, const int32_t *flags, const int32_t *len, int64_t n, double eps,
                                double *partial, unsigned long long *counts);
 __global__ void k_column_stats_final(const double *partial, double *frob2);
-__global__ void k_tau_fixed(const double *norm1, double tol, double *tau);
+__global__ void k_tau_fixed(const double *norm1, double tol, double *tau, int32_t nblocks);
 __global__ void k_scan_blocks(const int32_t *in, int64_t n, int64_t *out, int64_t *block_sums);
 __global__ void k_scan_sums(int64_t *block_sums, int64_t nb, int64_t *total);
 __global__ void k_scan_add(int64_t *out, int64_t n, const int64_t *block_sums, const int64_t *total);

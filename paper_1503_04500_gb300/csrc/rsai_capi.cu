@@ -26,8 +26,17 @@ struct rsai_handle {
     int64_t *row_ptr = nullptr, *col_ptr = nullptr, *csc_to_csr = nullptr;
     int32_t *col_idx = nullptr, *row_idx = nullptr;
     double *val = nullptr, *cval = nullptr;
-    // 8-byte words: norm1, tau_fixed, frob2, counters, column counts, partial sums
+    // 8-byte words: (unused), (unused), frob2, counters, column counts, partial sums
     unsigned long long *dscal = nullptr;
+    // blocks (a batch of independent matrices as one block-diagonal matrix)
+    int32_t nblocks = 1;
+    std::vector<int64_t> cstart_h{0};
+    int64_t *d_cstart = nullptr;
+    int32_t *col_block = nullptr;     // NULL for one block
+    double *norm1_arr = nullptr;      // ||A_b||_1 per block
+    double *tau_arr = nullptr;        // tol / ||A_b||_1 per block
+    double *bfrob2 = nullptr;         // per-block statistics
+    long long *bnc = nullptr, *bnnz = nullptr;
     int32_t *err = nullptr;
     uint32_t *qnext = nullptr;   // [3] queue counters, [3..4] overflow counts
     int32_t *ovf1 = nullptr, *ovf2 = nullptr;
@@ -111,8 +120,9 @@ DevParams dev_params(const rsai_handle *h) {
     P.eps = h->params.eps;
     P.tol = h->params.tol;
     P.tie_band = h->params.tie_band;
-    P.norm1 = dword(h, kNorm1);
-    P.tau_fixed = dword(h, kTau);
+    P.norm1 = h->norm1_arr;
+    P.tau_fixed = h->tau_arr;
+    P.col_block = h->col_block;
     return P;
 }
 
@@ -162,8 +172,9 @@ cudaError_t enqueue_build(rsai_handle *h, cudaStream_t st, cudaEvent_t *ev = nul
     cudaMemsetAsync(h->pool_top, 0, sizeof(unsigned long long), st);
     cudaMemsetAsync(h->row_count, 0, sizeof(int32_t) * (size_t)n, st);
     cudaMemsetAsync(h->cursor, 0, sizeof(int32_t) * (size_t)n, st);
-    k_norm1<<<blocks(n, 256), 256, 0, st>>>(h->col_ptr, h->cval, n, dword(h, kNorm1));
-    k_tau_fixed<<<1, 1, 0, st>>>(dword(h, kNorm1), h->params.tol, dword(h, kTau));
+    cudaMemsetAsync(h->norm1_arr, 0, sizeof(double) * (size_t)h->nblocks, st);
+    k_norm1<<<blocks(n, 256), 256, 0, st>>>(h->col_ptr, h->cval, n, h->col_block, h->norm1_arr);
+    k_tau_fixed<<<blocks(h->nblocks, 256), 256, 0, st>>>(h->norm1_arr, h->params.tol, h->tau_arr, h->nblocks);
 
     cudaError_t e = enqueue_bins(h, MODE_BUILD, dev_a(h), Frozen{}, h->dscal + kCtr, st, ev);
     if (e != cudaSuccess) return e;
@@ -286,52 +297,25 @@ void rsai_handle_free(rsai_handle *h) {
     delete h;
 }
 
-rsai_status rsai_build(const rsai_csr *A, const rsai_csc *Acsc, const rsai_params *params, void *stream,
-                       rsai_handle **out) {
-    if (!out) return RSAI_ERR_INVALID_ARG;
-    *out = nullptr;
-    int st_ = rsai_params_check(params);
-    if (st_ != RSAI_OK) return (rsai_status)st_;
-    st_ = check_csr_host(A);
-    if (st_ != RSAI_OK) return (rsai_status)st_;
-    if (!Acsc || !Acsc->col_ptr || !Acsc->row_idx || !Acsc->val) return RSAI_ERR_INVALID_ARG;
-    if (Acsc->n != A->n || Acsc->nnz != A->nnz) return RSAI_ERR_SHAPE;
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
-        cudaGetLastError();
-        return RSAI_ERR_NO_DEVICE;
-    }
-    cudaStream_t st = (cudaStream_t)stream;
-    rsai_handle *h = new (std::nothrow) rsai_handle();
-    if (!h) return RSAI_ERR_OOM;
-    h->alloc_stream = st;
-    cudaGetDevice(&h->device);
-    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
-    h->n = A->n;
-    h->nnz = A->nnz;
-    h->params = *params;
+}  // extern "C"
+
+namespace {
+
+// Everything after A (CSR, CSC, csc_to_csr space) and the block arrays are in
+// the handle: input checks, bins, buffers, the first build.  Returns OK or
+// WORKSPACE with a usable handle; any other status means failure.
+int build_common(rsai_handle *h, cudaStream_t st) {
     const int64_t n = h->n, nnz = h->nnz;
     int rc = RSAI_OK;
 #define TRY(x)                        \
     do {                              \
         rc = (x);                     \
-        if (rc != RSAI_OK) goto fail; \
+        if (rc != RSAI_OK) return rc; \
     } while (0)
-    TRY(dalloc(h, &h->row_ptr, n + 1, st));
-    TRY(dalloc(h, &h->col_ptr, n + 1, st));
-    TRY(dalloc(h, &h->col_idx, nnz, st));
-    TRY(dalloc(h, &h->row_idx, nnz, st));
-    TRY(dalloc(h, &h->val, nnz, st));
-    TRY(dalloc(h, &h->cval, nnz, st));
-    TRY(dalloc(h, &h->csc_to_csr, nnz, st));
-    TRY(cuda_status(to_device(h->row_ptr, A->row_ptr, sizeof(int64_t) * (n + 1), st)));
-    TRY(cuda_status(to_device(h->col_idx, A->col_idx, sizeof(int32_t) * nnz, st)));
-    TRY(cuda_status(to_device(h->val, A->val, sizeof(double) * nnz, st)));
-    TRY(cuda_status(to_device(h->col_ptr, Acsc->col_ptr, sizeof(int64_t) * (n + 1), st)));
-    TRY(cuda_status(to_device(h->row_idx, Acsc->row_idx, sizeof(int32_t) * nnz, st)));
-    TRY(cuda_status(to_device(h->cval, Acsc->val, sizeof(double) * nnz, st)));
     TRY(dalloc(h, &h->dscal, kScalars, st));
     TRY(dalloc(h, &h->err, 1, st));
+    TRY(dalloc(h, &h->norm1_arr, h->nblocks, st));
+    TRY(dalloc(h, &h->tau_arr, h->nblocks, st));
     // ---- validation of A (device kernels, error codes) ----
     {
         int32_t herr = 0;
@@ -369,6 +353,7 @@ rsai_status rsai_build(const rsai_csr *A, const rsai_csc *Acsc, const rsai_param
     h->scan_tmp_len = (n + 1023) / 1024 + 2;
     TRY(dalloc(h, &h->scan_tmp, h->scan_tmp_len, st));
     TRY(dalloc(h, &h->gwork, h->gstride * (size_t)h->grid_g, st));
+    int status = RSAI_OK;
     {
         // result pool: grows (and the build is repeated) if a column finds it full
         const int64_t g_est = std::max<int64_t>(32, 4 * (nnz / std::max<int64_t>(1, n)) + 16);
@@ -392,7 +377,7 @@ rsai_status rsai_build(const rsai_csr *A, const rsai_csc *Acsc, const rsai_param
             cudaMemcpyAsync(&herr, h->err, sizeof(herr), cudaMemcpyDeviceToHost, st);
             TRY(cuda_status(cudaStreamSynchronize(st)));
             if ((int64_t)top <= cap) {
-                if (herr != 0) rc = herr;
+                if (herr != 0) status = herr;
                 break;
             }
             // pool too small: release those buffers and retry with the size actually needed
@@ -418,13 +403,175 @@ rsai_status rsai_build(const rsai_csr *A, const rsai_csc *Acsc, const rsai_param
         }
     }
 #undef TRY
+    return status;
+}
+
+rsai_handle *new_handle(const rsai_params *params, cudaStream_t st) {
+    rsai_handle *h = new (std::nothrow) rsai_handle();
+    if (!h) return nullptr;
+    h->alloc_stream = st;
+    cudaGetDevice(&h->device);
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+    h->params = *params;
+    return h;
+}
+
+int have_device() {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return 0;
+    }
+    return 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+rsai_status rsai_build(const rsai_csr *A, const rsai_csc *Acsc, const rsai_params *params, void *stream,
+                       rsai_handle **out) {
+    if (!out) return RSAI_ERR_INVALID_ARG;
+    *out = nullptr;
+    int rc = rsai_params_check(params);
+    if (rc != RSAI_OK) return (rsai_status)rc;
+    rc = check_csr_host(A);
+    if (rc != RSAI_OK) return (rsai_status)rc;
+    if (!Acsc || !Acsc->col_ptr || !Acsc->row_idx || !Acsc->val) return RSAI_ERR_INVALID_ARG;
+    if (Acsc->n != A->n || Acsc->nnz != A->nnz) return RSAI_ERR_SHAPE;
+    if (!have_device()) return RSAI_ERR_NO_DEVICE;
+    cudaStream_t st = (cudaStream_t)stream;
+    rsai_handle *h = new_handle(params, st);
+    if (!h) return RSAI_ERR_OOM;
+    h->n = A->n;
+    h->nnz = A->nnz;
+    const int64_t n = h->n, nnz = h->nnz;
+    h->cstart_h = {0, n};
+    rc = dalloc(h, &h->row_ptr, n + 1, st);
+    if (rc == RSAI_OK) rc = dalloc(h, &h->col_ptr, n + 1, st);
+    if (rc == RSAI_OK) rc = dalloc(h, &h->col_idx, nnz, st);
+    if (rc == RSAI_OK) rc = dalloc(h, &h->row_idx, nnz, st);
+    if (rc == RSAI_OK) rc = dalloc(h, &h->val, nnz, st);
+    if (rc == RSAI_OK) rc = dalloc(h, &h->cval, nnz, st);
+    if (rc == RSAI_OK) rc = dalloc(h, &h->csc_to_csr, nnz, st);
+    if (rc == RSAI_OK) rc = dalloc(h, &h->d_cstart, 2, st);
+    if (rc == RSAI_OK) {
+        bool ok = to_device(h->row_ptr, A->row_ptr, sizeof(int64_t) * (n + 1), st) == cudaSuccess &&
+                  to_device(h->col_idx, A->col_idx, sizeof(int32_t) * nnz, st) == cudaSuccess &&
+                  to_device(h->val, A->val, sizeof(double) * nnz, st) == cudaSuccess &&
+                  to_device(h->col_ptr, Acsc->col_ptr, sizeof(int64_t) * (n + 1), st) == cudaSuccess &&
+                  to_device(h->row_idx, Acsc->row_idx, sizeof(int32_t) * nnz, st) == cudaSuccess &&
+                  to_device(h->cval, Acsc->val, sizeof(double) * nnz, st) == cudaSuccess &&
+                  cudaMemcpyAsync(h->d_cstart, h->cstart_h.data(), sizeof(int64_t) * 2, cudaMemcpyHostToDevice,
+                                  st) == cudaSuccess;
+        if (!ok) rc = RSAI_ERR_CUDA;
+    }
+    if (rc == RSAI_OK) rc = build_common(h, st);
+    if (rc != RSAI_OK && rc != RSAI_ERR_WORKSPACE) {
+        cudaStreamSynchronize(st);
+        cudaGetLastError();
+        rsai_handle_free(h);
+        return (rsai_status)rc;
+    }
     *out = h;
-    return (rsai_status)rc;  // OK, or WORKSPACE with failed columns flagged
-fail:
-    cudaStreamSynchronize(st);
-    cudaGetLastError();
-    rsai_handle_free(h);
     return (rsai_status)rc;
+}
+
+rsai_status rsai_build_batch(const rsai_csr *As, const rsai_csc *Acscs, int32_t count, const rsai_params *params,
+                             void *stream, rsai_handle **out) {
+    if (!out) return RSAI_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!As || !Acscs || count < 1) return RSAI_ERR_INVALID_ARG;
+    int rc = rsai_params_check(params);
+    if (rc != RSAI_OK) return (rsai_status)rc;
+    std::vector<int64_t> cstart(count + 1, 0), estart(count + 1, 0);
+    for (int b = 0; b < count; ++b) {
+        rc = check_csr_host(&As[b]);
+        if (rc != RSAI_OK) return (rsai_status)rc;
+        const rsai_csc &C = Acscs[b];
+        if (!C.col_ptr || !C.row_idx || !C.val) return RSAI_ERR_INVALID_ARG;
+        if (C.n != As[b].n || C.nnz != As[b].nnz) return RSAI_ERR_SHAPE;
+        cstart[b + 1] = cstart[b] + As[b].n;
+        estart[b + 1] = estart[b] + As[b].nnz;
+    }
+    if (cstart[count] > INT32_MAX) return RSAI_ERR_SHAPE;
+    if (!have_device()) return RSAI_ERR_NO_DEVICE;
+    cudaStream_t st = (cudaStream_t)stream;
+    rsai_handle *h = new_handle(params, st);
+    if (!h) return RSAI_ERR_OOM;
+    const int64_t n = cstart[count], nnz = estart[count];
+    h->n = n;
+    h->nnz = nnz;
+    h->nblocks = count;
+    h->cstart_h = cstart;
+    int64_t *d_estart = nullptr;
+    rc = dalloc(h, &h->row_ptr, n + 1, st);
+    if (rc == RSAI_OK) rc = dalloc(h, &h->col_ptr, n + 1, st);
+    if (rc == RSAI_OK) rc = dalloc(h, &h->col_idx, nnz, st);
+    if (rc == RSAI_OK) rc = dalloc(h, &h->row_idx, nnz, st);
+    if (rc == RSAI_OK) rc = dalloc(h, &h->val, nnz, st);
+    if (rc == RSAI_OK) rc = dalloc(h, &h->cval, nnz, st);
+    if (rc == RSAI_OK) rc = dalloc(h, &h->csc_to_csr, nnz, st);
+    if (rc == RSAI_OK) rc = dalloc(h, &h->d_cstart, count + 1, st);
+    if (rc == RSAI_OK) rc = dalloc(h, &d_estart, count + 1, st);
+    if (rc == RSAI_OK) rc = dalloc(h, &h->col_block, n, st);
+    for (int b = 0; rc == RSAI_OK && b < count; ++b) {
+        const rsai_csr &R = As[b];
+        const rsai_csc &C = Acscs[b];
+        const int64_t c0 = cstart[b], e0 = estart[b];
+        bool ok = to_device(h->row_ptr + c0, R.row_ptr, sizeof(int64_t) * R.n, st) == cudaSuccess &&
+                  to_device(h->col_idx + e0, R.col_idx, sizeof(int32_t) * R.nnz, st) == cudaSuccess &&
+                  to_device(h->val + e0, R.val, sizeof(double) * R.nnz, st) == cudaSuccess &&
+                  to_device(h->col_ptr + c0, C.col_ptr, sizeof(int64_t) * C.n, st) == cudaSuccess &&
+                  to_device(h->row_idx + e0, C.row_idx, sizeof(int32_t) * C.nnz, st) == cudaSuccess &&
+                  to_device(h->cval + e0, C.val, sizeof(double) * C.nnz, st) == cudaSuccess;
+        if (!ok) rc = RSAI_ERR_CUDA;
+    }
+    if (rc == RSAI_OK) {
+        cudaMemcpyAsync(h->d_cstart, cstart.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(d_estart, estart.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, st);
+        k_col_block<<<blocks(n, 256), 256, 0, st>>>(h->d_cstart, count, n, h->col_block);
+        k_shift_ptr<<<blocks(n + 1, 256), 256, 0, st>>>(h->row_ptr, n, h->col_block, d_estart, nnz);
+        k_shift_ptr<<<blocks(n + 1, 256), 256, 0, st>>>(h->col_ptr, n, h->col_block, d_estart, nnz);
+        k_shift_idx<<<blocks(n, 256), 256, 0, st>>>(h->row_ptr, h->col_idx, n, h->col_block, h->d_cstart);
+        k_shift_idx<<<blocks(n, 256), 256, 0, st>>>(h->col_ptr, h->row_idx, n, h->col_block, h->d_cstart);
+        if (cudaGetLastError() != cudaSuccess) rc = RSAI_ERR_CUDA;
+    }
+    if (rc == RSAI_OK) rc = build_common(h, st);
+    if (rc != RSAI_OK && rc != RSAI_ERR_WORKSPACE) {
+        cudaStreamSynchronize(st);
+        cudaGetLastError();
+        rsai_handle_free(h);
+        return (rsai_status)rc;
+    }
+    *out = h;
+    return (rsai_status)rc;
+}
+
+rsai_status rsai_get_block_stats(rsai_handle *h, void *stream, double *frob, int64_t *n_c, int64_t *nnz_M) {
+    if (!h) return RSAI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nb = h->nblocks;
+    if (!h->bfrob2) {
+        int rc = dalloc(h, &h->bfrob2, nb, st);
+        if (rc == RSAI_OK) rc = dalloc(h, &h->bnc, nb, st);
+        if (rc == RSAI_OK) rc = dalloc(h, &h->bnnz, nb, st);
+        if (rc != RSAI_OK) return (rsai_status)rc;
+    }
+    k_block_stats<<<nb, 256, 0, st>>>(h->d_cstart, h->rho, h->flags, h->col_len, h->params.eps, h->bfrob2, h->bnc,
+                                     h->bnnz);
+    std::vector<double> f2(nb);
+    std::vector<long long> c(nb), z(nb);
+    cudaMemcpyAsync(f2.data(), h->bfrob2, sizeof(double) * nb, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(c.data(), h->bnc, sizeof(long long) * nb, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(z.data(), h->bnnz, sizeof(long long) * nb, cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return RSAI_ERR_CUDA;
+    for (int b = 0; b < nb; ++b) {
+        if (frob) frob[b] = std::sqrt(f2[b]);
+        if (n_c) n_c[b] = c[b];
+        if (nnz_M) nnz_M[b] = z[b];
+    }
+    return RSAI_OK;
 }
 
 rsai_status rsai_set_values(rsai_handle *h, const double *A_val, void *stream) {
@@ -474,7 +621,13 @@ rsai_status rsai_get_stats(rsai_handle *h, void *stream, rsai_stats *out) {
     memset(out, 0, sizeof(*out));
     out->n = h->n;
     out->nnz_A = h->nnz;
-    out->norm1_A = dbl(kNorm1);
+    {
+        std::vector<double> nb((size_t)h->nblocks);
+        cudaMemcpy(nb.data(), h->norm1_arr, sizeof(double) * nb.size(), cudaMemcpyDeviceToHost);
+        double mx = 0.0;
+        for (double v : nb) mx = std::max(mx, v);
+        out->norm1_A = mx;
+    }
     out->qr_flops = (double)c[CTR_QR];
     out->res_flops = (double)c[CTR_RES];
     out->refine_flops = (double)c[CTR_REFINE];

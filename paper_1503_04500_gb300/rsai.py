@@ -32,7 +32,7 @@ EXPORTS = [
     "rsai_abi_version", "rsai_status_string", "rsai_params_default", "rsai_params_check", "rsai_build",
     "rsai_rebuild", "rsai_set_values", "rsai_get_stats", "rsai_get_M", "rsai_get_columns", "rsai_refit",
     "rsai_apply", "rsai_backward", "rsai_bicgstab", "rsai_handle_free", "rsai_peak_fma", "rsai_build_phase_times",
-    "rsai_bicgstab_noalloc",
+    "rsai_bicgstab_noalloc", "rsai_build_batch", "rsai_get_block_stats",
 ]
 
 
@@ -113,6 +113,9 @@ def load(build_if_missing: bool = False):
         "rsai_handle_free": (None, [vp]),
         "rsai_peak_fma": (i32, [i32, vp, ctypes.POINTER(f64)]),
         "rsai_build_phase_times": (i32, [vp, vp, ctypes.POINTER(f64)]),
+        "rsai_build_batch": (i32, [ctypes.POINTER(CSR), ctypes.POINTER(CSC), i32, ctypes.POINTER(Params), vp,
+                                   ctypes.POINTER(vp)]),
+        "rsai_get_block_stats": (i32, [vp, vp, vp, vp, vp]),
         "rsai_bicgstab_noalloc": (i32, [ctypes.POINTER(CSR), ctypes.POINTER(CSR), vp, vp, f64, i32,
                                         ctypes.POINTER(i32), ctypes.POINTER(f64), vp]),
     }
@@ -257,6 +260,15 @@ class Handle:
                "rsai_get_columns")
         return rho, loops, flags
 
+    def block_stats(self, count: int, stream=None):
+        """Per-member (||A_b M_b - I||_F, n_c, nnz(M_b)) of a batch handle."""
+        frob = np.zeros(count)
+        nc = np.zeros(count, np.int64)
+        nz = np.zeros(count, np.int64)
+        _check(load().rsai_get_block_stats(self._h, _stream(stream), _ptr(frob), _ptr(nc), _ptr(nz)),
+               "rsai_get_block_stats")
+        return frob, nc, nz
+
     def rebuild(self, stream=None):
         _check(load().rsai_rebuild(self._h, _stream(stream)), "rsai_rebuild")
 
@@ -318,6 +330,36 @@ def build(A, c=3, l_max=10, eps=0.3, drop="fixed", tol=1e-3, precision="fp64", t
             lib.rsai_handle_free(out)
         raise RSAIError(st, "rsai_build")
     return Handle(out.value, int(csr.n), params, st)
+
+
+def build_batch(members, c=3, l_max=10, eps=0.3, drop="fixed", tol=1e-3, precision="fp64", tie_band=1e-12,
+                stream=None, allow_failed=False) -> Handle:
+    """rsai_build_batch over a list of DeviceMatrix (device tensors) or
+    SparseMatrix-like (numpy, host) members; returns one handle whose M is
+    block diagonal."""
+    lib = load()
+    params = default_params(c=c, l_max=l_max, eps=eps, drop=drop, tol=tol, precision=precision, tie_band=tie_band)
+    csrs = (CSR * len(members))()
+    cscs = (CSC * len(members))()
+    keep = []
+    n = 0
+    for b, A in enumerate(members):
+        if isinstance(A, DeviceMatrix):
+            csrs[b], cscs[b] = A.csr(), A.csc()
+        else:
+            r, cc, k = _host_structs(A)
+            csrs[b], cscs[b] = r, cc
+            keep.append(k)
+        n += int(csrs[b].n)
+    out = ctypes.c_void_p(0)
+    st = lib.rsai_build_batch(csrs, cscs, len(members), ctypes.byref(params), _stream(stream), ctypes.byref(out))
+    del keep
+    ok = (RSAI_OK, 9) if allow_failed else (RSAI_OK,)
+    if st not in ok:
+        if out.value:
+            lib.rsai_handle_free(out)
+        raise RSAIError(st, "rsai_build_batch")
+    return Handle(out.value, n, params, st)
 
 
 def bicgstab(A: DeviceMatrix, M: Handle | None, b, rtol=1e-8, maxit=1000, stream=None):

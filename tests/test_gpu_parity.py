@@ -244,3 +244,29 @@ def test_peak_fma_positive():
     f32 = rsai.peak_fma(False)
     f64 = rsai.peak_fma(True)
     assert f32 > 1e12 and f64 > 1e10
+
+
+def test_batch_blocks_equal_member_builds():
+    """One block-diagonal batch build equals every member's own build, bit for bit."""
+    members = [gen.convdiff2d(12, (20.0, 20.0)), gen.powerlaw(700, seed=31, dmax=40),
+               gen.convdiff3d(6, peclet=3.0), gen.powerlaw(300, seed=32, dmax=25),
+               gen.convdiff2d(9, (-5.0, 13.0))]
+    kw = dict(c=3, l_max=10, eps=0.3, tol=1e-3, drop="fixed", precision="fp64")
+    hb = rsai.build_batch(members, **kw)
+    rp, ci, va = (t.cpu().numpy() for t in hb.M())
+    frob, nc, nz = hb.block_stats(len(members))
+    off = 0
+    for b, A in enumerate(members):
+        h = rsai.build(A, **kw)
+        mrp, mci, mva = (t.cpu().numpy() for t in h.M())
+        a0, a1 = rp[off], rp[off + A.n]
+        np.testing.assert_array_equal(rp[off:off + A.n + 1] - a0, mrp)
+        np.testing.assert_array_equal(ci[a0:a1] - off, mci)
+        np.testing.assert_array_equal(va[a0:a1], mva)
+        s = h.stats()
+        assert frob[b] == pytest.approx(s["frob"], rel=1e-13)
+        assert nz[b] == s["nnz_M"] and nc[b] == s["n_c"]
+        ref = oracle.build(A, **{k: v for k, v in kw.items() if k != "precision"})
+        assert frob[b] == pytest.approx(ref.frob(), rel=1e-10)
+        off += A.n
+        h.free()
