@@ -139,8 +139,12 @@ cudaError_t scan_counts(rsai_handle *h, const int32_t *in, int64_t *out, cudaStr
 
 // The three bins over all columns (mode: build, refit or backward); queue
 // counters are reset first.  `ev` (optional) brackets the bins (ev[1..4]).
+// `before_global` (optional, host side): called between bins C and G, e.g. to
+// size the global-bin slab from the number of columns that reached it.
+typedef int (*BinHook)(rsai_handle *h, cudaStream_t st);
+
 cudaError_t enqueue_bins(rsai_handle *h, int mode, const DevA &A, const Frozen &F, unsigned long long *gctr,
-                         cudaStream_t st, cudaEvent_t *ev = nullptr) {
+                         cudaStream_t st, cudaEvent_t *ev = nullptr, BinHook before_global = nullptr) {
     const int64_t n = h->n;
     cudaMemsetAsync(h->qnext, 0, sizeof(uint32_t) * 8, st);
     const DevParams P = dev_params(h);
@@ -156,6 +160,7 @@ cudaError_t enqueue_bins(rsai_handle *h, int mode, const DevA &A, const Frozen &
     if (ev) cudaEventRecord(ev[2], st);
     e = launch_bin_block(mode, fp32, h->grid_c, A, P, h->capC, QC, O, F, gctr, false, nullptr, 0, 1, st);
     if (e != cudaSuccess) return e;
+    if (before_global && before_global(h, st) != RSAI_OK) return cudaErrorMemoryAllocation;
     if (ev) cudaEventRecord(ev[3], st);
     e = launch_bin_block(mode, fp32, h->grid_g, A, P, h->capG, QG, O, F, gctr, true, h->gwork, h->gstride, 2, st);
     return e;
@@ -163,7 +168,7 @@ cudaError_t enqueue_bins(rsai_handle *h, int mode, const DevA &A, const Frozen &
 
 // The build sequence: no allocation, no host synchronisation (capturable).
 // `ev` (optional, RSAI_PHASE_COUNT + 1 events) are recorded between phases.
-cudaError_t enqueue_build(rsai_handle *h, cudaStream_t st, cudaEvent_t *ev = nullptr) {
+cudaError_t enqueue_build(rsai_handle *h, cudaStream_t st, cudaEvent_t *ev = nullptr, BinHook hook = nullptr) {
     const int64_t n = h->n;
     if (ev) cudaEventRecord(ev[0], st);
     cudaMemsetAsync(h->dscal, 0, sizeof(unsigned long long) * kScalars, st);
@@ -176,7 +181,7 @@ cudaError_t enqueue_build(rsai_handle *h, cudaStream_t st, cudaEvent_t *ev = nul
     k_norm1<<<blocks(n, 256), 256, 0, st>>>(h->col_ptr, h->cval, n, h->col_block, h->norm1_arr);
     k_tau_fixed<<<blocks(h->nblocks, 256), 256, 0, st>>>(h->norm1_arr, h->params.tol, h->tau_arr, h->nblocks);
 
-    cudaError_t e = enqueue_bins(h, MODE_BUILD, dev_a(h), Frozen{}, h->dscal + kCtr, st, ev);
+    cudaError_t e = enqueue_bins(h, MODE_BUILD, dev_a(h), Frozen{}, h->dscal + kCtr, st, ev, hook);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[4], st);
     k_column_stats<<<kStatBlocks, 256, 0, st>>>(h->rho, h->flags, h->col_len, n, h->params.eps,
@@ -234,9 +239,9 @@ int plan_bins(rsai_handle *h) {
     if (occ < 1) return RSAI_ERR_CUDA;
     h->grid_c = h->sms * occ;
     // bin G: a global-memory slab per CTA, one CTA per SM
-    h->capG = Caps{32768, 4096, 131072, 8192, (int64_t)1 << 22, 0};
+    h->capG = Caps{32768, 4096, 131072, 8192, (int64_t)1 << 24, 0};
     h->gstride = ((fp32 ? work_bytes<float>(h->capG) : work_bytes<double>(h->capG)) + 255) & ~size_t(255);
-    h->grid_g = std::min(h->sms, 8);  // grown after the first build if the tail needs it
+    h->grid_g = 1;  // sized by the first build (size_global_slab)
     return RSAI_OK;
 }
 
@@ -300,6 +305,24 @@ void rsai_handle_free(rsai_handle *h) {
 }  // extern "C"
 
 namespace {
+
+// One CTA of the global bin per column that reached it, up to one per SM: the
+// slab (a few tens of MB per CTA) is sized by the first build only.
+int size_global_slab(rsai_handle *h, cudaStream_t st) {
+    uint32_t cnt = 0;
+    if (cudaMemcpyAsync(&cnt, h->qnext + 4, sizeof(cnt), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return RSAI_ERR_CUDA;
+    const int want = std::max(1, std::min(h->sms, (int)cnt));
+    if (want <= h->grid_g) return RSAI_OK;
+    if (h->gwork) {
+        cudaFreeAsync(h->gwork, st);
+        h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void *)h->gwork), h->allocs.end());
+        h->gwork = nullptr;
+    }
+    h->grid_g = want;
+    return dalloc(h, &h->gwork, h->gstride * (size_t)h->grid_g, st);
+}
 
 // Everything after A (CSR, CSC, csc_to_csr space) and the block arrays are in
 // the handle: input checks, bins, buffers, the first build.  Returns OK or
@@ -370,7 +393,7 @@ int build_common(rsai_handle *h, cudaStream_t st) {
             TRY(dalloc(h, &h->tvals, cap, st));
             TRY(dalloc(h, &h->tsrc, cap, st));
             TRY(dalloc(h, &h->Mcsc_to_csr, cap, st));
-            TRY(cuda_status(enqueue_build(h, st)));
+            TRY(cuda_status(enqueue_build(h, st, nullptr, size_global_slab)));
             unsigned long long top = 0;
             int32_t herr = 0;
             cudaMemcpyAsync(&top, h->pool_top, sizeof(top), cudaMemcpyDeviceToHost, st);
@@ -388,18 +411,6 @@ int build_common(rsai_handle *h, cudaStream_t st) {
                 h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), p), h->allocs.end());
             }
             cap = std::min<int64_t>((int64_t)(top + top / 8 + 1024), n * n);
-        }
-    }
-    {
-        // many columns in the global bin: give it one CTA per SM for later rebuilds
-        unsigned long long cnt = 0;
-        cudaMemcpyAsync(&cnt, h->dscal + kCtr + CTR_COUNT + 2, sizeof(cnt), cudaMemcpyDeviceToHost, st);
-        TRY(cuda_status(cudaStreamSynchronize(st)));
-        if (cnt > 16ull * (unsigned long long)h->grid_g && h->grid_g < h->sms) {
-            cudaFreeAsync(h->gwork, st);
-            h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void *)h->gwork), h->allocs.end());
-            h->grid_g = h->sms;
-            TRY(dalloc(h, &h->gwork, h->gstride * (size_t)h->grid_g, st));
         }
     }
 #undef TRY
