@@ -39,7 +39,7 @@ struct Caps {
 };
 
 template <typename T> struct Work {
-    T *B, *vhead, *vtv, *rhs, *tmat;
+    T *B, *vhead, *vtv, *rhs;
     double *m, *r, *z, *wv;
     long long *ctr;
     int32_t *I, *S, *J, *Jn, *Rset, *buf, *buf2, *Rhat, *hkey, *hval;
@@ -50,7 +50,6 @@ template <typename T> struct Work {
         b += align16(sizeof(T) * (size_t)c.bcap);
         b += 2 * align16(sizeof(T) * (size_t)c.pcap);
         b += align16(sizeof(T) * (size_t)(c.qcap + 1));
-        b += align16(sizeof(T) * 256);
         b += align16(sizeof(double) * (size_t)c.pcap);
         b += align16(sizeof(double) * (size_t)(c.qcap + 1));
         b += align16(sizeof(double) * (size_t)c.pcap);
@@ -71,7 +70,6 @@ template <typename T> struct Work {
         vhead = (T *)(base + o); o += align16(sizeof(T) * (size_t)c.pcap);
         vtv = (T *)(base + o); o += align16(sizeof(T) * (size_t)c.pcap);
         rhs = (T *)(base + o); o += align16(sizeof(T) * (size_t)(c.qcap + 1));
-        tmat = (T *)(base + o); o += align16(sizeof(T) * 256);
         m = (double *)(base + o); o += align16(sizeof(double) * (size_t)c.pcap);
         r = (double *)(base + o); o += align16(sizeof(double) * (size_t)(c.qcap + 1));
         z = (double *)(base + o); o += align16(sizeof(double) * (size_t)c.pcap);
@@ -180,130 +178,6 @@ __device__ __noinline__ int qr_solve_team(Team team, T *B, int q, int p, T *rhs,
             vtvs[j] = vtv;
         }
         rank_flag |= (fabs(alpha) <= small) ? 1 : 0;
-        team.sync();
-    }
-    back_substitute_team(team, B, q, p, rhs, small);
-    return rank_flag;
-}
-
-// Blocked Householder QR (compact WY) for larger problems on a CTA team:
-// panels of kPanel columns are factored unblocked (the reflectors only touch
-// the panel), then T (upper triangular, H_1..H_nb = I - V T V^T) is formed and
-// every trailing column and the right-hand side get one update
-//   C <- C - V (T^T (V^T C)),
-// one warp per column, so the trailing matrix is streamed once per panel
-// instead of once per reflector.  Same reflectors, R and rhs as the unblocked
-// version (up to rounding); then back substitution.  Not inlined.
-constexpr int kPanel = 16;
-
-template <class Team, typename T>
-__device__ __noinline__ int qr_solve_blocked(Team team, T *B, int q, int p, T *rhs, T *vhead, T *vtvs, T small,
-                                             T *tmat /* kPanel*kPanel */) {
-    const int me = team.rank();
-    const int lane = me & 31, wid = me >> 5;
-    constexpr int NW = (Team::SIZE + 31) / 32;
-    int rank_flag = 0;
-    for (int j0 = 0; j0 < p; j0 += kPanel) {
-        const int nb = min(kPanel, p - j0);
-        // 1. panel
-        for (int j = j0; j < j0 + nb; ++j) {
-            T *col = B + (int64_t)j * q;
-            T part = 0;
-            for (int i = j + me; i < q; i += Team::SIZE) part += col[i] * col[i];
-            const T sigma = team.sum(part);
-            const T x0 = col[j];
-            const T nrm = sqrt(sigma);
-            const T alpha = (x0 >= T(0)) ? -nrm : nrm;
-            const T v0 = x0 - alpha;
-            const T vtv = sigma - x0 * x0 + v0 * v0;
-            if (vtv > T(0)) {
-                const T two_over = T(2) / vtv;
-                for (int c = j + 1 + wid; c < j0 + nb; c += NW) {
-                    T *t = B + (int64_t)c * q;
-                    T d = 0;
-                    for (int i = j + lane; i < q; i += 32) d += ((i == j) ? v0 : col[i]) * t[i];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-                    const T f = d * two_over;
-                    for (int i = j + lane; i < q; i += 32) t[i] -= f * ((i == j) ? v0 : col[i]);
-                }
-            }
-            team.sync();
-            if (me == 0) {
-                col[j] = alpha;
-                vhead[j] = v0;
-                vtvs[j] = vtv;
-            }
-            rank_flag |= (fabs(alpha) <= small) ? 1 : 0;
-            team.sync();
-        }
-        // reflector t of the panel, row i (zero above its head)
-        auto vat = [&](int t, int i) -> T {
-            const int jj = j0 + t;
-            return (i > jj) ? B[(int64_t)jj * q + i] : ((i == jj) ? vhead[jj] : T(0));
-        };
-        // 2. T: T_tt = tau_t, T(0:t, t) = -tau_t T(0:t, 0:t) (V(:,0:t)^T v_t)
-        for (int e = me; e < kPanel * kPanel; e += Team::SIZE) tmat[e] = T(0);
-        team.sync();
-        for (int pair = wid; pair < nb * nb; pair += NW) {  // y(s,t) = v_s^T v_t, s < t
-            const int s_ = pair / nb, t_ = pair % nb;
-            if (s_ >= t_) continue;
-            T d = 0;
-            for (int i = j0 + t_ + lane; i < q; i += 32) d += vat(s_, i) * vat(t_, i);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-            if (lane == 0) tmat[s_ * kPanel + t_] = d;  // holds y until the column is formed
-        }
-        team.sync();
-        if (me == 0) {
-            for (int t = 0; t < nb; ++t) {
-                const T vv = vtvs[j0 + t];
-                const T tau = (vv > T(0)) ? T(2) / vv : T(0);
-                T tmp[kPanel];
-                for (int r = 0; r < t; ++r) {
-                    T acc = 0;
-                    for (int s2 = r; s2 < t; ++s2) acc += tmat[r * kPanel + s2] * tmat[s2 * kPanel + t];
-                    tmp[r] = -tau * acc;
-                }
-                for (int r = 0; r < t; ++r) tmat[r * kPanel + t] = tmp[r];
-                tmat[t * kPanel + t] = tau;
-            }
-        }
-        team.sync();
-        // 3. trailing columns and rhs: C <- C - V (T^T (V^T C))
-        for (int c = j0 + nb + wid; c <= p; c += NW) {
-            T *t = (c < p) ? B + (int64_t)c * q : rhs;
-            T w[kPanel];
-#pragma unroll
-            for (int u = 0; u < kPanel; ++u) w[u] = T(0);
-            for (int i = j0 + lane; i < q; i += 32) {
-                const T ci = t[i];
-#pragma unroll
-                for (int u = 0; u < kPanel; ++u)
-                    if (u < nb) w[u] += vat(u, i) * ci;
-            }
-#pragma unroll
-            for (int u = 0; u < kPanel; ++u) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) w[u] += __shfl_xor_sync(0xffffffffu, w[u], o);
-            }
-            T w2[kPanel];
-#pragma unroll
-            for (int u = 0; u < kPanel; ++u) {
-                T acc = 0;
-#pragma unroll
-                for (int s2 = 0; s2 < kPanel; ++s2)
-                    if (s2 <= u && u < nb) acc += tmat[s2 * kPanel + u] * w[s2];
-                w2[u] = acc;
-            }
-            for (int i = j0 + lane; i < q; i += 32) {
-                T acc = t[i];
-#pragma unroll
-                for (int u = 0; u < kPanel; ++u)
-                    if (u < nb) acc -= vat(u, i) * w2[u];
-                t[i] = acc;
-            }
-        }
         team.sync();
     }
     back_substitute_team(team, B, q, p, rhs, small);
@@ -424,12 +298,6 @@ template <class Team, typename T> struct Column {
         if constexpr (std::is_same<Team, WarpTeam>::value) {
             if (p > 2 && p <= kSmallP && q <= kSmallQ) {
                 rank_flag = warp_qr_small(w.B, q, p, w.rhs, w.vhead, w.vtv, small);
-                return;
-            }
-        }
-        if constexpr (!std::is_same<Team, WarpTeam>::value) {
-            if (p >= 2 * kPanel) {
-                rank_flag = qr_solve_blocked<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.vtv, small, w.tmat);
                 return;
             }
         }
