@@ -183,6 +183,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the parametric 256^2 forward/adjoint measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -235,8 +237,12 @@ def main():
         torch.cuda.synchronize()
         return [a.elapsed_time(b) for a, b in ms]
 
+    from paper_1503_04500_gb300 import autotune
+
     h32 = rsai.build(dA, precision="fp32_refine", **PARAMS)
     h64 = rsai.build(dA, precision="fp64", **PARAMS)
+    tuned32 = autotune.tune(h32, A.nnz, "fp32_refine", steps=3)
+    tuned64 = autotune.tune(h64, A.nnz, "fp64", steps=2)
     for _ in range(args.warmup):
         flush.fill_(1.0)
         h32.rebuild()
@@ -358,6 +364,36 @@ def main():
         e2e = {"value": world * A.n / e2e_s, "unit": "columns/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s}
 
+    # parametric 2-D problem (256^2, A(theta) = L/h^2 + theta1 Cx + theta2 Cy): forward and adjoint
+    c4 = None
+    if args.extras:
+        P4 = inputs.parametric2d(256, (30.0, 10.0))
+        d4 = rsai.DeviceMatrix.from_host(P4.base)
+        c4 = {"workload": "parametric2d_256^2_theta(30,10)", "n": P4.base.n}
+        for prec in ("fp32_refine", "fp64"):
+            h4 = rsai.build(d4, precision=prec, **PARAMS)
+            autotune.tune(h4, P4.base.nnz, prec, steps=2)
+            f_ms = statistics.median(timed(h4, 5))
+            nnz4 = h4.stats()["nnz_M"]
+            gM = torch.zeros(nnz4, dtype=torch.float64, device="cuda")
+            gr = torch.ones(P4.base.n, dtype=torch.float64, device="cuda")
+            h4.backward(d4.val, gM, gr)
+            st4 = torch.cuda.current_stream()
+            bt = []
+            for _ in range(5):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st4)
+                h4.backward(d4.val, gM, gr)
+                e1.record(st4)
+                torch.cuda.synchronize()
+                bt.append(e0.elapsed_time(e1))
+            b_ms = statistics.median(bt)
+            c4[prec] = {"fwd_ms": f_ms, "bwd_ms": b_ms, "bwd_fwd_ratio": b_ms / f_ms,
+                        "columns_per_s": P4.base.n / (f_ms / 1e3), "frob": h4.stats()["frob"]}
+            h4.free()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -381,6 +417,8 @@ def main():
         "bwd_fwd_ratio": bwd32 / dev_ms,
         "bwd_ms": bwd32, "bwd_fwd_ratio_fp64": bwd64 / dev_ms64,
         "roofline": roof32, "phases_ms": ph32,
+        "tuning": {"fp32_refine": tuned32["tuning"], "fp64": tuned64["tuning"]},
+        "parametric2d_256": c4,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": KERNELS_PER_BUILD * args.steps,
         "wall_s_timed_region": t_wall,

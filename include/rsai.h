@@ -288,6 +288,25 @@ rsai_status rsai_build_phase_times(rsai_handle *h, void *stream, double *ms);
 rsai_status rsai_bicgstab_noalloc(const rsai_csr *A, const rsai_csr *M, const double *b, double *x, double rtol,
                                   int32_t maxit, int32_t *iters, double *relres, void *stream);
 
+/*
+ * Launch shapes of the size bins.  They change speed only: every column of M
+ * is computed by the same arithmetic whatever the shape, so results are
+ * identical bit for bit.  Picked per GPU and problem by the autotuner of the
+ * Python package (paper_1503_04500_gb300/autotune.py).
+ */
+typedef struct {
+    int32_t warp_bin_warps;       /* warps per CTA of the warp bin: 1, 2, 4 or 8 (default 4) */
+    int32_t warp_bin_ctas_per_sm; /* resident CTAs per SM of the warp bin, 0 = as many as fit */
+    int32_t small_qr_max_p;       /* largest |J| solved by the register-resident warp QR, 0..16 (16) */
+    int32_t global_bin_ctas;      /* CTAs of the global bin, 0 = one per column that reaches it, <= SMs */
+} rsai_tuning;
+
+/* Read / replace a handle's launch shapes; the next rsai_rebuild records a new
+ * graph.  Synchronises the handle's stream.  Errors: INVALID_ARG (a value out
+ * of range or a shape that cannot be resident), OOM. */
+rsai_status rsai_get_tuning(const rsai_handle *h, rsai_tuning *t);
+rsai_status rsai_set_tuning(rsai_handle *h, const rsai_tuning *t);
+
 /* Release a handle and its device memory (NULL is a no-op). */
 void rsai_handle_free(rsai_handle *h);
 

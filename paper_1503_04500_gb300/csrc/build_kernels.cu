@@ -277,7 +277,7 @@ __device__ void run_queue(const Team &team, Work<T> &w, const DevA &A, const Dev
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(128, (sizeof(T) == 8 ? 2 : 4))
+__global__ void __launch_bounds__(256, (sizeof(T) == 8 ? 1 : 2))
     k_bin_warp(DevA A, DevParams P, Caps cap, ColQueue Q, ColOut O, Frozen F, unsigned long long *gctr, int last_bin) {
     extern __shared__ __align__(16) char smem[];
     const int wid = threadIdx.x >> 5;

@@ -36,6 +36,7 @@ struct Caps {
     int rcap;      // max |R| (dominant rows used so far)
     int64_t bcap;  // max q*p elements of B
     int hcap;      // slots of the J -> position hash (power of two >= 2*pcap), 0 = none
+    int small_p;   // largest |J| solved by the register-resident warp QR (0: never)
 };
 
 template <typename T> struct Work {
@@ -296,7 +297,7 @@ template <class Team, typename T> struct Column {
     // into rhs[0..p); the reflectors stay in B (tails), vhead and vtv.
     __device__ void qr_solve(T small) {
         if constexpr (std::is_same<Team, WarpTeam>::value) {
-            if (p > 2 && p <= kSmallP && q <= kSmallQ) {
+            if (p > 2 && p <= cap.small_p && q <= kSmallQ) {
                 rank_flag = warp_qr_small(w.B, q, p, w.rhs, w.vhead, w.vtv, small);
                 return;
             }
@@ -307,7 +308,7 @@ template <class Team, typename T> struct Column {
     // rhs <- R^{-1} Q^T rhs with the stored reflectors
     __device__ void apply_qt_solve(T small) {
         if constexpr (std::is_same<Team, WarpTeam>::value) {
-            if (p > 2 && p <= kSmallP && q <= kSmallQ) {
+            if (p > 2 && p <= cap.small_p && q <= kSmallQ) {
                 warp_apply_qt_small(w.B, q, p, w.rhs, w.vhead, w.vtv, small);
                 return;
             }

@@ -63,6 +63,7 @@ struct rsai_handle {
     // bins
     Caps capW{}, capC{}, capG{};
     int grid_w = 0, grid_c = 0;
+    rsai_tuning tuning{4, 0, kSmallP, 0};
     // refit / backward scratch (allocated on first use)
     double *fval = nullptr, *fcval = nullptr;
     int64_t *qoff = nullptr, *Mcsr_to_csc = nullptr;
@@ -155,7 +156,8 @@ cudaError_t enqueue_bins(rsai_handle *h, int mode, const DevA &A, const Frozen &
     ColQueue QC{h->ovf1, h->qnext + 3, n, h->qnext + 1, h->ovf2, h->qnext + 4, h->ovf_cap};
     ColQueue QG{h->ovf2, h->qnext + 4, n, h->qnext + 2, nullptr, nullptr, 0};
     if (ev) cudaEventRecord(ev[1], st);
-    cudaError_t e = launch_bin_warp(mode, fp32, h->grid_w, kWarpsPerCta, A, P, h->capW, QW, O, F, gctr, false, st);
+    cudaError_t e = launch_bin_warp(mode, fp32, h->grid_w, h->tuning.warp_bin_warps, A, P, h->capW, QW, O, F, gctr,
+                                    false, st);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], st);
     e = launch_bin_block(mode, fp32, h->grid_c, A, P, h->capC, QC, O, F, gctr, false, nullptr, 0, 1, st);
@@ -224,12 +226,13 @@ int plan_bins(rsai_handle *h) {
     int dev = h->device, max_optin = 0;
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int rneed = std::max(64, h->params.c * std::max(1, h->params.l_max));
-    h->capW = Caps{64, 32, 256, 64, 64 * 32, 64};
-    int occ = occupancy_bin_warp(fp32, kWarpsPerCta, h->capW);
+    h->capW = Caps{64, 32, 256, 64, 64 * 32, 64, h->tuning.small_qr_max_p};
+    int occ = occupancy_bin_warp(fp32, h->tuning.warp_bin_warps, h->capW);
     if (occ < 1) return RSAI_ERR_CUDA;
+    if (h->tuning.warp_bin_ctas_per_sm > 0) occ = std::min(occ, h->tuning.warp_bin_ctas_per_sm);
     h->grid_w = h->sms * occ;
     // bin C: shared-memory workspace as large as the opt-in limit allows
-    Caps c{1024, 256, 4096, std::min(rneed * 2, 2048), 0, 0};
+    Caps c{1024, 256, 4096, std::min(rneed * 2, 2048), 0, 0, 0};
     size_t base = fp32 ? work_bytes<float>(c) : work_bytes<double>(c);
     size_t avail = (size_t)max_optin - 2048;
     if (base >= avail) return RSAI_ERR_CUDA;
@@ -239,7 +242,7 @@ int plan_bins(rsai_handle *h) {
     if (occ < 1) return RSAI_ERR_CUDA;
     h->grid_c = h->sms * occ;
     // bin G: a global-memory slab per CTA, one CTA per SM
-    h->capG = Caps{32768, 4096, 131072, 8192, (int64_t)1 << 24, 0};
+    h->capG = Caps{32768, 4096, 131072, 8192, (int64_t)1 << 24, 0, 0};
     h->gstride = ((fp32 ? work_bytes<float>(h->capG) : work_bytes<double>(h->capG)) + 255) & ~size_t(255);
     h->grid_g = 1;  // sized by the first build (size_global_slab)
     return RSAI_OK;
@@ -313,7 +316,8 @@ int size_global_slab(rsai_handle *h, cudaStream_t st) {
     if (cudaMemcpyAsync(&cnt, h->qnext + 4, sizeof(cnt), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return RSAI_ERR_CUDA;
-    const int want = std::max(1, std::min(h->sms, (int)cnt));
+    int want = std::max(1, std::min(h->sms, (int)cnt));
+    if (h->tuning.global_bin_ctas > 0) want = std::min(h->tuning.global_bin_ctas, h->sms);
     if (want <= h->grid_g) return RSAI_OK;
     if (h->gwork) {
         cudaFreeAsync(h->gwork, st);
@@ -821,6 +825,53 @@ rsai_status rsai_backward(rsai_handle *h, const double *A_val, const double *gra
                               st) != cudaSuccess)
         return RSAI_ERR_CUDA;
     return (rsai_status)finish_frozen(h, st);
+}
+
+rsai_status rsai_get_tuning(const rsai_handle *h, rsai_tuning *t) {
+    if (!h || !t) return RSAI_ERR_INVALID_ARG;
+    *t = h->tuning;
+    return RSAI_OK;
+}
+
+rsai_status rsai_set_tuning(rsai_handle *h, const rsai_tuning *t) {
+    if (!h || !t) return RSAI_ERR_INVALID_ARG;
+    const int w = t->warp_bin_warps;
+    if (w != 1 && w != 2 && w != 4 && w != 8) return RSAI_ERR_INVALID_ARG;
+    if (t->warp_bin_ctas_per_sm < 0 || t->small_qr_max_p < 0 || t->small_qr_max_p > kSmallP ||
+        t->global_bin_ctas < 0)
+        return RSAI_ERR_INVALID_ARG;
+    cudaStream_t st = h->alloc_stream;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return RSAI_ERR_CUDA;
+    const rsai_tuning old = h->tuning;
+    h->tuning = *t;
+    const bool fp32 = h->params.precision == RSAI_FP32_REFINE;
+    h->capW.small_p = t->small_qr_max_p;
+    int occ = occupancy_bin_warp(fp32, w, h->capW);
+    if (occ < 1) {
+        h->tuning = old;
+        h->capW.small_p = old.small_qr_max_p;
+        return RSAI_ERR_INVALID_ARG;
+    }
+    if (t->warp_bin_ctas_per_sm > 0) occ = std::min(occ, t->warp_bin_ctas_per_sm);
+    h->grid_w = h->sms * occ;
+    if (t->global_bin_ctas > 0) {
+        const int want = std::min(t->global_bin_ctas, h->sms);
+        if (want > h->grid_g) {
+            if (h->gwork) {
+                cudaFreeAsync(h->gwork, st);
+                h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void *)h->gwork), h->allocs.end());
+                h->gwork = nullptr;
+            }
+            int rc = dalloc(h, &h->gwork, h->gstride * (size_t)want, st);
+            if (rc != RSAI_OK) return (rsai_status)rc;
+        }
+        h->grid_g = want;
+    }
+    if (h->graph) {  // the launch shapes are part of the recorded graph
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    return RSAI_OK;
 }
 
 rsai_status rsai_build_phase_times(rsai_handle *h, void *stream, double *ms) {

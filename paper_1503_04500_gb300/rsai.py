@@ -32,7 +32,7 @@ EXPORTS = [
     "rsai_abi_version", "rsai_status_string", "rsai_params_default", "rsai_params_check", "rsai_build",
     "rsai_rebuild", "rsai_set_values", "rsai_get_stats", "rsai_get_M", "rsai_get_columns", "rsai_refit",
     "rsai_apply", "rsai_backward", "rsai_bicgstab", "rsai_handle_free", "rsai_peak_fma", "rsai_build_phase_times",
-    "rsai_bicgstab_noalloc", "rsai_build_batch", "rsai_get_block_stats",
+    "rsai_bicgstab_noalloc", "rsai_build_batch", "rsai_get_block_stats", "rsai_get_tuning", "rsai_set_tuning",
 ]
 
 
@@ -56,6 +56,14 @@ class Params(ctypes.Structure):
     _fields_ = [("c", ctypes.c_int32), ("l_max", ctypes.c_int32), ("eps", ctypes.c_double),
                 ("drop_mode", ctypes.c_int32), ("tol", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("tie_band", ctypes.c_double), ("flags", ctypes.c_uint32)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("warp_bin_warps", ctypes.c_int32), ("warp_bin_ctas_per_sm", ctypes.c_int32),
+                ("small_qr_max_p", ctypes.c_int32), ("global_bin_ctas", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class Stats(ctypes.Structure):
@@ -116,6 +124,8 @@ def load(build_if_missing: bool = False):
         "rsai_build_batch": (i32, [ctypes.POINTER(CSR), ctypes.POINTER(CSC), i32, ctypes.POINTER(Params), vp,
                                    ctypes.POINTER(vp)]),
         "rsai_get_block_stats": (i32, [vp, vp, vp, vp, vp]),
+        "rsai_get_tuning": (i32, [vp, ctypes.POINTER(Tuning)]),
+        "rsai_set_tuning": (i32, [vp, ctypes.POINTER(Tuning)]),
         "rsai_bicgstab_noalloc": (i32, [ctypes.POINTER(CSR), ctypes.POINTER(CSR), vp, vp, f64, i32,
                                         ctypes.POINTER(i32), ctypes.POINTER(f64), vp]),
     }
@@ -268,6 +278,16 @@ class Handle:
         _check(load().rsai_get_block_stats(self._h, _stream(stream), _ptr(frob), _ptr(nc), _ptr(nz)),
                "rsai_get_block_stats")
         return frob, nc, nz
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        _check(load().rsai_get_tuning(self._h, ctypes.byref(t)), "rsai_get_tuning")
+        return t.as_dict()
+
+    def set_tuning(self, **kw):
+        """rsai_set_tuning: launch shapes of the bins (speed only, identical results)."""
+        t = Tuning(**{**self.tuning(), **kw})
+        _check(load().rsai_set_tuning(self._h, ctypes.byref(t)), "rsai_set_tuning")
 
     def rebuild(self, stream=None):
         _check(load().rsai_rebuild(self._h, _stream(stream)), "rsai_rebuild")

@@ -270,3 +270,33 @@ def test_batch_blocks_equal_member_builds():
         assert frob[b] == pytest.approx(ref.frob(), rel=1e-10)
         off += A.n
         h.free()
+
+
+def test_tuning_changes_speed_not_results(c1):
+    """Every launch shape computes the same M bit for bit."""
+    P = gen.powerlaw(1500, seed=41, dmax=40)
+    for A, kw in ((c1, PARAMS_C1), (P, dict(c=5, l_max=8, eps=0.4, tol=1e-3))):
+        for precision in ("fp64", "fp32_refine"):
+            dA = rsai.DeviceMatrix.from_host(A)
+            h = rsai.build(dA, precision=precision, drop="fixed", **kw)
+            ref = [t.clone() for t in h.M()]
+            for tun in (dict(warp_bin_warps=1), dict(warp_bin_warps=8, small_qr_max_p=0),
+                        dict(warp_bin_warps=2, warp_bin_ctas_per_sm=1, small_qr_max_p=8, global_bin_ctas=3)):
+                h.set_tuning(**tun)
+                h.rebuild()
+                for a, b in zip(ref, h.M()):
+                    assert torch.equal(a, b), (precision, tun)
+            h.free()
+
+
+def test_autotuner_picks_and_caches(tmp_path, c1):
+    from paper_1503_04500_gb300 import autotune
+
+    dA = rsai.DeviceMatrix.from_host(c1)
+    h = rsai.build(dA, precision="fp32_refine", **PARAMS_C1)
+    path = str(tmp_path / "tuning.json")
+    res = autotune.tune(h, c1.nnz, "fp32_refine", steps=2, path=path)
+    assert not res["cached"] and len(res["trials"]) >= 3
+    assert h.tuning() == res["tuning"]
+    again = autotune.tune(h, c1.nnz, "fp32_refine", steps=2, path=path)
+    assert again["cached"] and again["tuning"] == res["tuning"]
