@@ -289,10 +289,13 @@ rsai_status rsai_bicgstab_noalloc(const rsai_csr *A, const rsai_csr *M, const do
                                   int32_t maxit, int32_t *iters, double *relres, void *stream);
 
 /*
- * Launch shapes of the size bins.  They change speed only: every column of M
- * is computed by the same arithmetic whatever the shape, so results are
- * identical bit for bit.  Picked per GPU and problem by the autotuner of the
- * Python package (paper_1503_04500_gb300/autotune.py).
+ * Launch shapes of the size bins.  The CTA shapes and grid sizes change speed
+ * only: every column is computed by the same arithmetic whatever the shape, so
+ * M is identical bit for bit.  small_qr_max_p chooses between the
+ * register-resident and the shared-memory Householder QR of the warp bin, which
+ * agree to rounding (same patterns in practice, values within ~1e-14 relative
+ * in FP64).  Picked per GPU and problem by the autotuner of the Python package
+ * (paper_1503_04500_gb300/autotune.py).
  */
 typedef struct {
     int32_t warp_bin_warps;       /* warps per CTA of the warp bin: 1, 2, 4 or 8 (default 4) */
