@@ -310,24 +310,29 @@ __global__ void k_invert_map(const int64_t *map, int64_t n, int64_t *inv) {
     if (e < n) inv[map[e]] = e;
 }
 
-__global__ void k_adjoint_gather(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const int64_t *Mrowptr,
-                                 const int32_t *Mcols, const int64_t *Mcsr_to_csc, const int64_t *qoff,
-                                 const int32_t *poolI, const double *poolR, const double *poolW,
-                                 const double *alphaM, const double *xM, double *grad) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-        const int32_t j = col_idx[e];
-        double acc = 0.0;
-        for (int64_t f = Mrowptr[j]; f < Mrowptr[j + 1]; ++f) {
-            const int32_t kk = Mcols[f];
-            const int64_t ce = Mcsr_to_csc[f];
-            const int64_t a = qoff[kk];
-            const int pos = find_i32(poolI + a, (int)(qoff[kk + 1] - a), (int32_t)i);
-            if (pos >= 0) acc += poolR[a + pos] * alphaM[ce] - poolW[a + pos] * xM[ce];
-        }
-        grad[e] = acc;
+__global__ void k_adjoint_gather(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col_idx,
+                                 const int64_t *Mrowptr, const int32_t *Mcols, const int64_t *Mcsr_to_csc,
+                                 const int64_t *qoff, const int32_t *poolI, const double *poolR,
+                                 const double *poolW, const double *alphaM, const double *xM, double *grad) {
+    // one thread per nonzero A(i,j) (CSR position e); its row by binary search
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nnz) return;
+    int64_t lo = 0, hi = n;  // last row with row_ptr[row] <= e
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (row_ptr[mid] <= e) lo = mid; else hi = mid;
     }
+    const int32_t i = (int32_t)lo;
+    const int32_t j = col_idx[e];
+    double acc = 0.0;
+    for (int64_t f = Mrowptr[j]; f < Mrowptr[j + 1]; ++f) {
+        const int32_t kk = Mcols[f];
+        const int64_t ce = Mcsr_to_csc[f];
+        const int64_t a = qoff[kk];
+        const int pos = find_i32(poolI + a, (int)(qoff[kk + 1] - a), i);
+        if (pos >= 0) acc += poolR[a + pos] * alphaM[ce] - poolW[a + pos] * xM[ce];
+    }
+    grad[e] = acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -550,8 +555,13 @@ cudaError_t launch_adjoint_gather(int64_t n, int64_t nnzM, const int64_t *row_pt
                                   const double *poolR, const double *poolW, const double *alphaM,
                                   const double *xM, double *grad, cudaStream_t st) {
     if (nnzM > 0) k_invert_map<<<(unsigned)((nnzM + 255) / 256), 256, 0, st>>>(Mcsc_to_csr, nnzM, Mcsr_to_csc);
-    k_adjoint_gather<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, row_ptr, col_idx, Mrowptr, Mcols, Mcsr_to_csc,
-                                                                   qoff, poolI, poolR, poolW, alphaM, xM, grad);
+    int64_t nnzA = 0;
+    cudaMemcpyAsync(&nnzA, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return cudaGetLastError();
+    if (nnzA > 0)
+        k_adjoint_gather<<<(unsigned)((nnzA + 255) / 256), 256, 0, st>>>(n, nnzA, row_ptr, col_idx, Mrowptr, Mcols,
+                                                                        Mcsr_to_csc, qoff, poolI, poolR, poolW,
+                                                                        alphaM, xM, grad);
     return cudaGetLastError();
 }
 

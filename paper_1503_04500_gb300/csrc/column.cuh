@@ -778,6 +778,38 @@ template <class Team, typename T> struct Column {
         return true;
     }
 
+    // First solve, J = {k} (Eq. 2.3 with p = 1): I = rows of A(:,k), which the
+    // CSC keeps ascending, and m_kk = a_kk / ||a_k||^2 in double (the closed
+    // form of the 1-column LS problem; no sort, tile or QR needed).
+    __device__ bool initial_solve() {
+        const int me = team.rank();
+        const int64_t e0 = A.col_ptr[k];
+        const int len = (int)(A.col_ptr[k + 1] - e0);
+        if (len > cap.qcap) return false;
+        double nn = 0.0, akk = 0.0;
+        for (int i = me; i < len; i += Team::SIZE) {
+            const int32_t r = A.row_idx[e0 + i];
+            const double a = A.cval[e0 + i];
+            w.I[i] = r;
+            nn = fma(a, a, nn);
+            if (r == k) akk = a;
+        }
+        nn = team.sum(nn);
+        akk = team.sum(akk);
+        q = len;
+        build_jhash();
+        if (me == 0) w.m[0] = (nn > 0.0) ? akk / nn : 0.0;
+        rank_flag = (nn > 0.0) ? 0 : 1;
+        c_qr += solve_flops(0, 0, q, 1);
+        q0 = q;
+        p0 = 1;
+        c_solves += 1;
+        c_pmax = max(c_pmax, 1);
+        c_qmax = max(c_qmax, q);
+        team.sync();
+        return true;
+    }
+
     __device__ int run() {
         const int me = team.rank();
         p = 1; q = 0; s = 0; nR = 0; l = 0; q0 = 0; p0 = 0; rank_flag = 0; rho = 0.0;
@@ -789,10 +821,15 @@ template <class Team, typename T> struct Column {
         // One solve site: the first pass of every round solves on the new J
         // (appended to the last factor after the first round), the second
         // re-solves after a drop (Eq. 4.3); then the residual (Eq. 2.4).
-        bool append = false;
+        bool append = false, first = true;
         for (;;) {
             for (int pass = 0; pass < 2; ++pass) {
-                if (!solve(append)) return COL_OVERFLOW;
+                if (first) {
+                    if (!initial_solve()) return COL_OVERFLOW;
+                    first = false;
+                } else if (!solve(append)) {
+                    return COL_OVERFLOW;
+                }
                 append = false;
                 if (pass == 1 || !drop()) break;
             }
