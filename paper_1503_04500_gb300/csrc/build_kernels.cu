@@ -295,8 +295,12 @@ __global__ void __launch_bounds__(NT, 1)
     __shared__ unsigned long long red[NT / 32 + 1];
     __shared__ int redi[NT / 32 + 1];
     Work<T> w;
-    if (gwork) w.carve(gwork + (size_t)blockIdx.x * gstride, cap);
-    else w.carve(smem, cap);
+    if (gwork) {
+        w.carve(gwork + (size_t)blockIdx.x * gstride, cap);
+        w.stage = smem;  // shared memory is free for panel staging
+    } else {
+        w.carve(smem, cap);
+    }
     BlockTeam<NT> team{red, redi};
     run_queue<MODE>(team, w, A, P, cap, Q, O, F, gctr, last_bin != 0, bin);
 }
@@ -514,7 +518,7 @@ template <typename T, int MODE>
 static cudaError_t launch_block_t(int grid, const DevA &A, const DevParams &P, const Caps &cap, const ColQueue &Q,
                                   const ColOut &O, const Frozen &F, unsigned long long *gctr, bool last, char *gwork,
                                   size_t gstride, int bin, cudaStream_t st) {
-    size_t smem = gwork ? 0 : Work<T>::bytes(cap);
+    size_t smem = gwork ? (size_t)cap.stage_bytes : Work<T>::bytes(cap);
     cudaFuncSetAttribute(k_bin_block<T, kBlockThreads, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_bin_block<T, kBlockThreads, MODE><<<grid, kBlockThreads, smem, st>>>(A, P, cap, Q, O, F, gctr, last ? 1 : 0,
                                                                           gwork, gstride, bin);

@@ -37,6 +37,7 @@ struct Caps {
     int64_t bcap;  // max q*p elements of B
     int hcap;      // slots of the J -> position hash (power of two >= 2*pcap), 0 = none
     int small_p;   // largest |J| solved by the register-resident warp QR (0: never)
+    int stage_bytes;  // shared memory for staging QR panels (global-memory bins), 0 = none
 };
 
 template <typename T> struct Work {
@@ -44,6 +45,7 @@ template <typename T> struct Work {
     double *m, *r, *z, *wv;
     long long *ctr;
     int32_t *I, *S, *J, *Jn, *Rset, *buf, *buf2, *Rhat, *hkey, *hval;
+    char *stage = nullptr;  // panel staging area (shared memory), not part of the carved workspace
 
     __host__ __device__ static size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
     __host__ __device__ static size_t bytes(const Caps &c) {
@@ -144,42 +146,207 @@ __device__ void back_substitute_team(const Team &team, const T *B, int q, int p,
 // each warp forming its column's dot product with the reflector (lanes over
 // rows, one warp reduction) and applying the update itself, so a step costs
 // one team synchronisation instead of one per column.  Not inlined.
+// One Householder step j on B (q x p, ld q) and rhs: the reflector of column j
+// over rows >= j, applied to the columns c in [c_begin, p) and to rhs.  The
+// norm is one team reduction; the columns are dealt out to the team's warps,
+// each warp forming its column's dot product (lanes over rows, one warp
+// reduction) and applying the update itself.  Stores R_jj, v_j(j), v_j^T v_j.
 template <class Team, typename T>
-__device__ __noinline__ int qr_solve_team(Team team, T *B, int q, int p, T *rhs, T *vhead, T *vtvs, T small) {
+__device__ __forceinline__ void householder_step(const Team &team, T *B, int q, int p, T *rhs, T *vhead, T *vtvs,
+                                                 int j, int c_begin, T small, int &rank_flag) {
     const int me = team.rank();
     const int lane = me & 31, wid = me >> 5;
     constexpr int NW = (Team::SIZE + 31) / 32;
-    int rank_flag = 0;
-    for (int j = 0; j < p; ++j) {
-        T *col = B + (int64_t)j * q;
-        T part = 0;
-        for (int i = j + me; i < q; i += Team::SIZE) part += col[i] * col[i];
-        const T sigma = team.sum(part);
-        const T x0 = col[j];
-        const T nrm = sqrt(sigma);
-        const T alpha = (x0 >= T(0)) ? -nrm : nrm;
-        const T v0 = x0 - alpha;
-        const T vtv = sigma - x0 * x0 + v0 * v0;
-        if (vtv > T(0)) {
-            const T two_over = T(2) / vtv;
-            for (int c = j + 1 + wid; c <= p; c += NW) {
-                T *t = (c < p) ? B + (int64_t)c * q : rhs;
-                T d = 0;
-                for (int i = j + lane; i < q; i += 32) d += ((i == j) ? v0 : col[i]) * t[i];
+    T *col = B + (int64_t)j * q;
+    T part = 0;
+    for (int i = j + me; i < q; i += Team::SIZE) part += col[i] * col[i];
+    const T sigma = team.sum(part);
+    const T x0 = col[j];
+    const T nrm = sqrt(sigma);
+    const T alpha = (x0 >= T(0)) ? -nrm : nrm;
+    const T v0 = x0 - alpha;
+    const T vtv = sigma - x0 * x0 + v0 * v0;
+    if (vtv > T(0)) {
+        const T two_over = T(2) / vtv;
+        for (int c = c_begin + wid; c <= p; c += NW) {
+            T *t = (c < p) ? B + (int64_t)c * q : rhs;
+            T d = 0;
+            for (int i = j + lane; i < q; i += 32) d += ((i == j) ? v0 : col[i]) * t[i];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-                const T f = d * two_over;
-                for (int i = j + lane; i < q; i += 32) t[i] -= f * ((i == j) ? v0 : col[i]);
+            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            const T f = d * two_over;
+            for (int i = j + lane; i < q; i += 32) t[i] -= f * ((i == j) ? v0 : col[i]);
+        }
+    }
+    team.sync();
+    if (me == 0) {
+        col[j] = alpha;
+        vhead[j] = v0;
+        vtvs[j] = vtv;
+    }
+    rank_flag |= (fabs(alpha) <= small) ? 1 : 0;
+    team.sync();
+}
+
+// Householder QR of B (q x p, column-major, ld q) applied to rhs, then back
+// substitution into rhs[0..p).  Keeps the reflectors (v_j below the diagonal
+// of B, heads in vhead, v^T v in vtv) for the refinement solve.  Returns the
+// rank flag.  Team-generic, one team synchronisation per step; not inlined.
+template <class Team, typename T>
+__device__ __noinline__ int qr_solve_team(Team team, T *B, int q, int p, T *rhs, T *vhead, T *vtvs, T small) {
+    int rank_flag = 0;
+    for (int j = 0; j < p; ++j) householder_step(team, B, q, p, rhs, vhead, vtvs, j, j + 1, small, rank_flag);
+    back_substitute_team(team, B, q, p, rhs, small);
+    return rank_flag;
+}
+
+// Blocked Householder QR (compact WY) for the bins whose workspace is in
+// global memory.  Panels of nb <= kPanel columns (nb chosen so that rows j0..q
+// of the panel fit the shared-memory staging area) are copied to shared
+// memory, factored there, written back, and turned into explicit reflectors V
+// (zeros above the head, v(j) on the diagonal); with T upper triangular,
+// H_1...H_nb = I - V T V^T, every trailing column and the right-hand side get
+//   C <- C - V (T^T (V^T C))
+// in one pass (one warp per column), so the trailing matrix in global memory
+// is streamed once per panel instead of once per reflector.  A panel that does
+// not fit four columns falls back to single Householder steps.  The
+// reflectors, R and rhs are those of the unblocked version up to rounding.
+constexpr int kPanel = 16;
+
+template <class Team, typename T>
+__device__ __noinline__ int qr_solve_staged(Team team, T *B, int q, int p, T *rhs, T *vhead, T *vtvs, T small,
+                                            T *stage, int stage_bytes) {
+    const int me = team.rank();
+    const int lane = me & 31, wid = me >> 5;
+    constexpr int NW = (Team::SIZE + 31) / 32;
+    T *tm = stage;                     // kPanel x kPanel
+    T *V = stage + kPanel * kPanel;    // panel, ld = q - j0
+    const int64_t velems = (int64_t)stage_bytes / (int64_t)sizeof(T) - kPanel * kPanel;
+    int rank_flag = 0;
+    int j0 = 0;
+    while (j0 < p) {
+        const int qq = q - j0;
+        int nb = (int)min((int64_t)kPanel, velems / (int64_t)max(qq, 1));
+        nb = min(nb, p - j0);
+        if (nb < 4) {
+            householder_step(team, B, q, p, rhs, vhead, vtvs, j0, j0 + 1, small, rank_flag);
+            ++j0;
+            continue;
+        }
+        // 1. stage rows j0..q-1 of the panel columns
+        for (int idx = me; idx < nb * qq; idx += Team::SIZE) {
+            const int t = idx / qq, r = idx - t * qq;
+            V[idx] = B[(int64_t)(j0 + t) * q + j0 + r];
+        }
+        team.sync();
+        // 2. factor the panel in shared memory (local rows r = i - j0)
+        for (int t = 0; t < nb; ++t) {
+            T *col = V + (int64_t)t * qq;
+            T part = 0;
+            for (int r = t + me; r < qq; r += Team::SIZE) part += col[r] * col[r];
+            const T sigma = team.sum(part);
+            const T x0 = col[t];
+            const T nrm = sqrt(sigma);
+            const T alpha = (x0 >= T(0)) ? -nrm : nrm;
+            const T v0 = x0 - alpha;
+            const T vtv = sigma - x0 * x0 + v0 * v0;
+            if (vtv > T(0)) {
+                const T two_over = T(2) / vtv;
+                for (int c = t + 1 + wid; c < nb; c += NW) {
+                    T *cc = V + (int64_t)c * qq;
+                    T d = 0;
+                    for (int r = t + lane; r < qq; r += 32) d += ((r == t) ? v0 : col[r]) * cc[r];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                    const T f = d * two_over;
+                    for (int r = t + lane; r < qq; r += 32) cc[r] -= f * ((r == t) ? v0 : col[r]);
+                }
+            }
+            team.sync();
+            if (me == 0) {
+                col[t] = alpha;
+                vhead[j0 + t] = v0;
+                vtvs[j0 + t] = vtv;
+            }
+            rank_flag |= (fabs(alpha) <= small) ? 1 : 0;
+            team.sync();
+        }
+        // 3. panel back to B (R entries and reflector tails), 4. explicit V
+        for (int idx = me; idx < nb * qq; idx += Team::SIZE) {
+            const int t = idx / qq, r = idx - t * qq;
+            B[(int64_t)(j0 + t) * q + j0 + r] = V[idx];
+        }
+        team.sync();
+        for (int idx = me; idx < nb * qq; idx += Team::SIZE) {
+            const int t = idx / qq, r = idx - t * qq;
+            if (r < t) V[idx] = T(0);
+            else if (r == t) V[idx] = vhead[j0 + t];
+        }
+        for (int e = me; e < kPanel * kPanel; e += Team::SIZE) tm[e] = T(0);
+        team.sync();
+        // 5. T: y(s,t) = v_s^T v_t (s < t), then column by column
+        //    T(t,t) = tau_t, T(0:t, t) = -tau_t T(0:t, 0:t) y(0:t, t)
+        for (int pair = wid; pair < nb * nb; pair += NW) {
+            const int s_ = pair / nb, t_ = pair - s_ * nb;
+            if (s_ >= t_) continue;
+            const T *vs = V + (int64_t)s_ * qq, *vt = V + (int64_t)t_ * qq;
+            T d = 0;
+            for (int r = t_ + lane; r < qq; r += 32) d += vs[r] * vt[r];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            if (lane == 0) tm[s_ * kPanel + t_] = d;
+        }
+        team.sync();
+        for (int t = 0; t < nb; ++t) {
+            const T vv = vtvs[j0 + t];
+            const T tau = (vv > T(0)) ? T(2) / vv : T(0);
+            T val = T(0);
+            if (me < t) {
+                T acc = 0;
+                for (int s2 = me; s2 < t; ++s2) acc += tm[me * kPanel + s2] * tm[s2 * kPanel + t];
+                val = -tau * acc;
+            }
+            team.sync();
+            if (me < t) tm[me * kPanel + t] = val;
+            if (me == t) tm[t * kPanel + t] = tau;
+            team.sync();
+        }
+        // 6. trailing columns and rhs: C <- C - V (T^T (V^T C)), rows j0..q-1
+        for (int c = j0 + nb + wid; c <= p; c += NW) {
+            T *tc = ((c < p) ? B + (int64_t)c * q : rhs) + j0;
+            T wv[kPanel];
+#pragma unroll
+            for (int u = 0; u < kPanel; ++u) wv[u] = T(0);
+            for (int r = lane; r < qq; r += 32) {
+                const T cr = tc[r];
+#pragma unroll
+                for (int u = 0; u < kPanel; ++u)
+                    if (u < nb) wv[u] += V[(int64_t)u * qq + r] * cr;
+            }
+#pragma unroll
+            for (int u = 0; u < kPanel; ++u) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) wv[u] += __shfl_xor_sync(0xffffffffu, wv[u], o);
+            }
+            T w2[kPanel];
+#pragma unroll
+            for (int u = 0; u < kPanel; ++u) {
+                T acc = 0;
+#pragma unroll
+                for (int s2 = 0; s2 < kPanel; ++s2)
+                    if (s2 <= u && u < nb) acc += tm[s2 * kPanel + u] * wv[s2];
+                w2[u] = acc;
+            }
+            for (int r = lane; r < qq; r += 32) {
+                T acc = tc[r];
+#pragma unroll
+                for (int u = 0; u < kPanel; ++u)
+                    if (u < nb) acc -= V[(int64_t)u * qq + r] * w2[u];
+                tc[r] = acc;
             }
         }
         team.sync();
-        if (me == 0) {
-            col[j] = alpha;
-            vhead[j] = v0;
-            vtvs[j] = vtv;
-        }
-        rank_flag |= (fabs(alpha) <= small) ? 1 : 0;
-        team.sync();
+        j0 += nb;
     }
     back_substitute_team(team, B, q, p, rhs, small);
     return rank_flag;
@@ -299,6 +466,13 @@ template <class Team, typename T> struct Column {
         if constexpr (std::is_same<Team, WarpTeam>::value) {
             if (p > 2 && p <= cap.small_p && q <= kSmallQ) {
                 rank_flag = warp_qr_small(w.B, q, p, w.rhs, w.vhead, w.vtv, small);
+                return;
+            }
+        }
+        if constexpr (!std::is_same<Team, WarpTeam>::value) {
+            if (cap.stage_bytes > 0 && p >= 2 * kPanel) {
+                rank_flag = qr_solve_staged<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.vtv, small, (T *)w.stage,
+                                                     cap.stage_bytes);
                 return;
             }
         }

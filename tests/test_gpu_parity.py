@@ -103,7 +103,7 @@ def test_powerlaw_all_bins(precision):
     kw = dict(c=5, l_max=8, eps=0.4, tol=1e-3, drop="fixed")
     h, dA, res, rho, loops, flags, st = gpu_M(P, precision=precision, **kw)
     ref = oracle.build(P, **kw)
-    assert st["cols_bin"][1] + st["cols_bin"][2] > 0
+    assert st["cols_bin"][1] > 0 and st["cols_bin"][2] > 0  # CTA bin and global bin (blocked QR) both used
     assert sum(st["cols_bin"]) == P.n
     assert st["n_failed"] == 0
     if precision == "fp64":
