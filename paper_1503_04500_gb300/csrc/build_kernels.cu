@@ -73,6 +73,12 @@ __global__ void k_norm1(const int64_t *col_ptr, const double *cval, int64_t n, c
     atomicMax((unsigned long long *)&out[b], (unsigned long long)__double_as_longlong(s));
 }
 
+// columns flagged FAILED (e.g. the result pool was full), for a second run
+__global__ void k_collect_failed(const int32_t *flags, int64_t n, int32_t *list, uint32_t *count) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n && (flags[k] & RSAI_COL_FAILED)) list[atomicAdd(count, 1u)] = (int32_t)k;
+}
+
 // block of every column from the block start offsets
 __global__ void k_col_block(const int64_t *cstart, int32_t nblocks, int64_t n, int32_t *col_block) {
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;

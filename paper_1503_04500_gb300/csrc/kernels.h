@@ -16,6 +16,7 @@ __global__ void k_csc_map(DevA A, int64_t *csc_to_csr, int32_t *err);
 __global__ void k_csc_from_csr(const double *csr_val, const int64_t *csc_to_csr, double *cval, int64_t nnz);
 __global__ void k_norm1(const int64_t *col_ptr, const double *cval, int64_t n, const int32_t *col_block,
                         double *out);
+__global__ void k_collect_failed(const int32_t *flags, int64_t n, int32_t *list, uint32_t *count);
 __global__ void k_col_block(const int64_t *cstart, int32_t nblocks, int64_t n, int32_t *col_block);
 __global__ void k_shift_ptr(int64_t *ptr, int64_t n, const int32_t *col_block, const int64_t *estart,
                             int64_t nnz_total);

@@ -145,14 +145,15 @@ cudaError_t scan_counts(rsai_handle *h, const int32_t *in, int64_t *out, cudaStr
 typedef int (*BinHook)(rsai_handle *h, cudaStream_t st);
 
 cudaError_t enqueue_bins(rsai_handle *h, int mode, const DevA &A, const Frozen &F, unsigned long long *gctr,
-                         cudaStream_t st, cudaEvent_t *ev = nullptr, BinHook before_global = nullptr) {
+                         cudaStream_t st, cudaEvent_t *ev = nullptr, BinHook before_global = nullptr,
+                         const int32_t *wlist = nullptr, const uint32_t *wcount = nullptr) {
     const int64_t n = h->n;
-    cudaMemsetAsync(h->qnext, 0, sizeof(uint32_t) * 8, st);
+    cudaMemsetAsync(h->qnext, 0, sizeof(uint32_t) * 5, st);  // queue and overflow counters; [5] = retry count
     const DevParams P = dev_params(h);
     const bool fp32 = h->params.precision == RSAI_FP32_REFINE;
     ColOut O{h->col_off, h->col_len, h->col_q, h->rho, h->loops, h->flags, h->pool_rows, h->pool_vals,
              h->pool_cap, h->pool_top, h->err};
-    ColQueue QW{nullptr, nullptr, n, h->qnext + 0, h->ovf1, h->qnext + 3, h->ovf_cap};
+    ColQueue QW{wlist, wcount, n, h->qnext + 0, h->ovf1, h->qnext + 3, h->ovf_cap};
     ColQueue QC{h->ovf1, h->qnext + 3, n, h->qnext + 1, h->ovf2, h->qnext + 4, h->ovf_cap};
     ColQueue QG{h->ovf2, h->qnext + 4, n, h->qnext + 2, nullptr, nullptr, 0};
     if (ev) cudaEventRecord(ev[1], st);
@@ -170,6 +171,8 @@ cudaError_t enqueue_bins(rsai_handle *h, int mode, const DevA &A, const Frozen &
 
 // The build sequence: no allocation, no host synchronisation (capturable).
 // `ev` (optional, RSAI_PHASE_COUNT + 1 events) are recorded between phases.
+cudaError_t enqueue_build_tail(rsai_handle *h, cudaStream_t st, cudaEvent_t *ev);
+
 cudaError_t enqueue_build(rsai_handle *h, cudaStream_t st, cudaEvent_t *ev = nullptr, BinHook hook = nullptr) {
     const int64_t n = h->n;
     if (ev) cudaEventRecord(ev[0], st);
@@ -186,6 +189,13 @@ cudaError_t enqueue_build(rsai_handle *h, cudaStream_t st, cudaEvent_t *ev = nul
     cudaError_t e = enqueue_bins(h, MODE_BUILD, dev_a(h), Frozen{}, h->dscal + kCtr, st, ev, hook);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[4], st);
+    return enqueue_build_tail(h, st, ev);
+}
+
+// statistics and the assembly of M (the end of the build sequence)
+cudaError_t enqueue_build_tail(rsai_handle *h, cudaStream_t st, cudaEvent_t *ev) {
+    const int64_t n = h->n;
+    cudaError_t e;
     k_column_stats<<<kStatBlocks, 256, 0, st>>>(h->rho, h->flags, h->col_len, n, h->params.eps,
                                                 dword(h, kPartial), h->dscal + kCounts);
     k_column_stats_final<<<1, kStatBlocks, 0, st>>>(dword(h, kPartial), dword(h, kFrob2));
@@ -382,39 +392,69 @@ int build_common(rsai_handle *h, cudaStream_t st) {
     TRY(dalloc(h, &h->gwork, h->gstride * (size_t)h->grid_g, st));
     int status = RSAI_OK;
     {
-        // result pool: grows (and the build is repeated) if a column finds it full
-        const int64_t g_est = std::max<int64_t>(32, 4 * (nnz / std::max<int64_t>(1, n)) + 16);
+        // result pool: if columns find it full, it grows (keeping what was
+        // written) and only those columns run again
+        const int64_t g_est = std::max<int64_t>(32, 6 * (nnz / std::max<int64_t>(1, n)) + 16);
         int64_t cap = std::min<int64_t>(n * g_est, n * n);
+        h->pool_cap = cap;
+        TRY(dalloc(h, &h->pool_rows, cap, st));
+        TRY(dalloc(h, &h->pool_vals, cap, st));
+        auto alloc_m = [&](int64_t c) -> int {
+            int r = dalloc(h, &h->Mrows, c, st);
+            if (r == RSAI_OK) r = dalloc(h, &h->Mvals_csc, c, st);
+            if (r == RSAI_OK) r = dalloc(h, &h->Mcols, c, st);
+            if (r == RSAI_OK) r = dalloc(h, &h->Mvals, c, st);
+            if (r == RSAI_OK) r = dalloc(h, &h->tcols, c, st);
+            if (r == RSAI_OK) r = dalloc(h, &h->tvals, c, st);
+            if (r == RSAI_OK) r = dalloc(h, &h->tsrc, c, st);
+            if (r == RSAI_OK) r = dalloc(h, &h->Mcsc_to_csr, c, st);
+            return r;
+        };
+        auto release = [&](void *p) {
+            cudaFreeAsync(p, st);
+            h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), p), h->allocs.end());
+        };
+        TRY(alloc_m(cap));
+        TRY(cuda_status(enqueue_build(h, st, nullptr, size_global_slab)));
+        int32_t *retry = nullptr;
         for (int attempt = 0; attempt < 6; ++attempt) {
-            h->pool_cap = cap;
-            TRY(dalloc(h, &h->pool_rows, cap, st));
-            TRY(dalloc(h, &h->pool_vals, cap, st));
-            TRY(dalloc(h, &h->Mrows, cap, st));
-            TRY(dalloc(h, &h->Mvals_csc, cap, st));
-            TRY(dalloc(h, &h->Mcols, cap, st));
-            TRY(dalloc(h, &h->Mvals, cap, st));
-            TRY(dalloc(h, &h->tcols, cap, st));
-            TRY(dalloc(h, &h->tvals, cap, st));
-            TRY(dalloc(h, &h->tsrc, cap, st));
-            TRY(dalloc(h, &h->Mcsc_to_csr, cap, st));
-            TRY(cuda_status(enqueue_build(h, st, nullptr, size_global_slab)));
             unsigned long long top = 0;
             int32_t herr = 0;
             cudaMemcpyAsync(&top, h->pool_top, sizeof(top), cudaMemcpyDeviceToHost, st);
             cudaMemcpyAsync(&herr, h->err, sizeof(herr), cudaMemcpyDeviceToHost, st);
             TRY(cuda_status(cudaStreamSynchronize(st)));
-            if ((int64_t)top <= cap) {
+            if ((int64_t)top <= h->pool_cap) {
                 if (herr != 0) status = herr;
                 break;
             }
-            // pool too small: release those buffers and retry with the size actually needed
-            void *pool_bufs[] = {h->pool_rows, h->pool_vals, h->Mrows, h->Mvals_csc, h->Mcols,
-                                 h->Mvals, h->tcols, h->tvals, h->tsrc, h->Mcsc_to_csr};
-            for (void *p : pool_bufs) {
-                cudaFreeAsync(p, st);
-                h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), p), h->allocs.end());
-            }
-            cap = std::min<int64_t>((int64_t)(top + top / 8 + 1024), n * n);
+            // grow the pool (copying what fits), M's buffers with it
+            const int64_t old_cap = h->pool_cap;
+            // new reservations start at `top`; the columns to redo need at most `top`
+            cap = std::min<int64_t>((int64_t)(2 * top + 1024), std::max<int64_t>(n * n, (int64_t)top + 1024));
+            int32_t *nrows = nullptr;
+            double *nvals = nullptr;
+            TRY(dalloc(h, &nrows, cap, st));
+            TRY(dalloc(h, &nvals, cap, st));
+            cudaMemcpyAsync(nrows, h->pool_rows, sizeof(int32_t) * old_cap, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(nvals, h->pool_vals, sizeof(double) * old_cap, cudaMemcpyDeviceToDevice, st);
+            void *old_bufs[] = {h->pool_rows, h->pool_vals, h->Mrows, h->Mvals_csc, h->Mcols,
+                                h->Mvals, h->tcols, h->tvals, h->tsrc, h->Mcsc_to_csr};
+            for (void *p : old_bufs) release(p);
+            h->pool_rows = nrows;
+            h->pool_vals = nvals;
+            h->pool_cap = cap;
+            TRY(alloc_m(cap));
+            // the columns that found the pool full run again (from its current top)
+            if (!retry) TRY(dalloc(h, &retry, n, st));
+            cudaMemsetAsync(h->qnext + 5, 0, sizeof(uint32_t), st);
+            k_collect_failed<<<blocks(n, 256), 256, 0, st>>>(h->flags, n, retry, h->qnext + 5);
+            cudaMemsetAsync(h->dscal + kCtr + CTR_FAILED, 0, sizeof(unsigned long long), st);
+            cudaMemsetAsync(h->err, 0, sizeof(int32_t), st);
+            cudaMemsetAsync(h->row_count, 0, sizeof(int32_t) * (size_t)n, st);
+            cudaMemsetAsync(h->cursor, 0, sizeof(int32_t) * (size_t)n, st);
+            TRY(cuda_status(enqueue_bins(h, MODE_BUILD, dev_a(h), Frozen{}, h->dscal + kCtr, st, nullptr,
+                                         size_global_slab, retry, h->qnext + 5)));
+            TRY(cuda_status(enqueue_build_tail(h, st, nullptr)));
         }
     }
 #undef TRY

@@ -308,3 +308,21 @@ def test_autotuner_picks_and_caches(tmp_path, c1):
     assert h.tuning() == res["tuning"]
     again = autotune.tune(h, c1.nnz, "fp32_refine", steps=2, path=path)
     assert again["cached"] and again["tuning"] == res["tuning"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_pool_overflow_reruns_only_failed_columns(precision):
+    """nnz(M)/n = 174 here, above the first pool estimate (52 per column): the pool grows and the
+    columns that found it full run again; M still matches the oracle."""
+    P = gen.powerlaw(600, seed=5, dmax=40)
+    kw = dict(c=5, l_max=6, eps=0.05, drop="none")
+    h, dA, res, rho, loops, flags, st = gpu_M(P, precision=precision, **kw)
+    ref = oracle.build(P, **kw)
+    assert st["n_failed"] == 0 and st["nnz_M"] > 52 * P.n
+    if precision == "fp64":
+        assert_fp64_parity(P, ref, res, rho, loops, flags, st, rtol=1e-9)
+    else:
+        cp, rows, _ = csc_from_csr(*res, P.n)
+        same = np.array([np.array_equal(rows[cp[k]:cp[k + 1]], ref.column(k)[0]) for k in range(P.n)])
+        assert same.mean() >= 0.99
+        np.testing.assert_allclose(rho[same], ref.rho[same], rtol=1e-5)
