@@ -196,6 +196,7 @@ cudaError_t enqueue_build(rsai_handle *h, cudaStream_t st, cudaEvent_t *ev = nul
 cudaError_t enqueue_build_tail(rsai_handle *h, cudaStream_t st, cudaEvent_t *ev) {
     const int64_t n = h->n;
     cudaError_t e;
+    cudaMemsetAsync(h->dscal + kCounts, 0, sizeof(unsigned long long) * 2, st);  // n_c, nnz(M): accumulated
     k_column_stats<<<kStatBlocks, 256, 0, st>>>(h->rho, h->flags, h->col_len, n, h->params.eps,
                                                 dword(h, kPartial), h->dscal + kCounts);
     k_column_stats_final<<<1, kStatBlocks, 0, st>>>(dword(h, kPartial), dword(h, kFrob2));
