@@ -311,38 +311,68 @@ __device__ __noinline__ int qr_solve_staged(Team team, T *B, int q, int p, T *rh
             if (me == t) tm[t * kPanel + t] = tau;
             team.sync();
         }
-        // 6. trailing columns and rhs: C <- C - V (T^T (V^T C)), rows j0..q-1
-        for (int c = j0 + nb + wid; c <= p; c += NW) {
-            T *tc = ((c < p) ? B + (int64_t)c * q : rhs) + j0;
-            T wv[kPanel];
+        // 6. trailing columns and rhs: C <- C - V (T^T (V^T C)), rows j0..q-1;
+        //    each warp takes kCols columns at a time so that every reflector
+        //    value read from shared memory serves kCols columns
+        constexpr int kCols = 4;
+        for (int c0 = j0 + nb + wid * kCols; c0 <= p; c0 += NW * kCols) {
+            T *tc[kCols];
 #pragma unroll
-            for (int u = 0; u < kPanel; ++u) wv[u] = T(0);
+            for (int x = 0; x < kCols; ++x) {
+                const int c = c0 + x;
+                tc[x] = (c < p) ? B + (int64_t)c * q + j0 : ((c == p) ? rhs + j0 : nullptr);
+            }
+            T wv[kCols][kPanel];
+#pragma unroll
+            for (int x = 0; x < kCols; ++x)
+#pragma unroll
+                for (int u = 0; u < kPanel; ++u) wv[x][u] = T(0);
             for (int r = lane; r < qq; r += 32) {
-                const T cr = tc[r];
+                T cr[kCols];
+#pragma unroll
+                for (int x = 0; x < kCols; ++x) cr[x] = tc[x] ? tc[x][r] : T(0);
+#pragma unroll
+                for (int u = 0; u < kPanel; ++u) {
+                    if (u < nb) {
+                        const T v = V[(int64_t)u * qq + r];
+#pragma unroll
+                        for (int x = 0; x < kCols; ++x) wv[x][u] += v * cr[x];
+                    }
+                }
+            }
+#pragma unroll
+            for (int x = 0; x < kCols; ++x)
 #pragma unroll
                 for (int u = 0; u < kPanel; ++u)
-                    if (u < nb) wv[u] += V[(int64_t)u * qq + r] * cr;
-            }
 #pragma unroll
-            for (int u = 0; u < kPanel; ++u) {
+                    for (int o = 16; o > 0; o >>= 1) wv[x][u] += __shfl_xor_sync(0xffffffffu, wv[x][u], o);
+            // w2 = T^T w (kept in wv, highest u first so that lower entries are still w)
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) wv[u] += __shfl_xor_sync(0xffffffffu, wv[u], o);
-            }
-            T w2[kPanel];
+            for (int x = 0; x < kCols; ++x) {
 #pragma unroll
-            for (int u = 0; u < kPanel; ++u) {
-                T acc = 0;
+                for (int u = kPanel - 1; u >= 0; --u) {
+                    T acc = 0;
 #pragma unroll
-                for (int s2 = 0; s2 < kPanel; ++s2)
-                    if (s2 <= u && u < nb) acc += tm[s2 * kPanel + u] * wv[s2];
-                w2[u] = acc;
+                    for (int s2 = 0; s2 <= u; ++s2)
+                        if (u < nb) acc += tm[s2 * kPanel + u] * wv[x][s2];
+                    wv[x][u] = acc;
+                }
             }
             for (int r = lane; r < qq; r += 32) {
-                T acc = tc[r];
+                T acc[kCols];
 #pragma unroll
-                for (int u = 0; u < kPanel; ++u)
-                    if (u < nb) acc -= V[(int64_t)u * qq + r] * w2[u];
-                tc[r] = acc;
+                for (int x = 0; x < kCols; ++x) acc[x] = tc[x] ? tc[x][r] : T(0);
+#pragma unroll
+                for (int u = 0; u < kPanel; ++u) {
+                    if (u < nb) {
+                        const T v = V[(int64_t)u * qq + r];
+#pragma unroll
+                        for (int x = 0; x < kCols; ++x) acc[x] -= v * wv[x][u];
+                    }
+                }
+#pragma unroll
+                for (int x = 0; x < kCols; ++x)
+                    if (tc[x]) tc[x][r] = acc[x];
             }
         }
         team.sync();
