@@ -38,6 +38,7 @@ struct Caps {
     int hcap;      // slots of the J -> position hash (power of two >= 2*pcap), 0 = none
     int small_p;   // largest |J| solved by the register-resident warp QR (0: never)
     int stage_bytes;  // shared memory for staging QR panels (global-memory bins), 0 = none
+    int append;       // CTA bins: keep the factor between loops and append to it (Section 3)
 };
 
 template <typename T> struct Work {
@@ -45,6 +46,8 @@ template <typename T> struct Work {
     double *m, *r, *z, *wv;
     long long *ctr;
     int32_t *I, *S, *J, *Jn, *Rset, *buf, *buf2, *Rhat, *hkey, *hval;
+    int32_t *Ip, *Jp;  // factor position of each sorted I / J entry (Caps::append)
+    T *qte;            // Q^T e_k(I) of the kept factor, factor row order (Caps::append)
     char *stage = nullptr;  // panel staging area (shared memory), not part of the carved workspace
 
     __host__ __device__ static size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -65,6 +68,11 @@ template <typename T> struct Work {
         b += 2 * align16(sizeof(int32_t) * (size_t)c.scap);
         b += align16(sizeof(int32_t) * 32);
         b += 2 * align16(sizeof(int32_t) * (size_t)c.hcap);
+        if (c.append) {
+            b += align16(sizeof(int32_t) * (size_t)c.qcap);
+            b += align16(sizeof(int32_t) * (size_t)c.pcap);
+            b += align16(sizeof(T) * (size_t)(c.qcap + 1));
+        }
         return b;
     }
     __device__ void carve(char *base, const Caps &c) {
@@ -88,6 +96,13 @@ template <typename T> struct Work {
         Rhat = (int32_t *)(base + o); o += align16(sizeof(int32_t) * 32);
         hkey = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.hcap);
         hval = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.hcap);
+        Ip = Jp = nullptr;
+        qte = nullptr;
+        if (c.append) {
+            Ip = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.qcap);
+            Jp = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.pcap);
+            qte = (T *)(base + o); o += align16(sizeof(T) * (size_t)(c.qcap + 1));
+        }
     }
 };
 
@@ -200,6 +215,131 @@ __device__ __noinline__ int qr_solve_team(Team team, T *B, int q, int p, T *rhs,
     return rank_flag;
 }
 
+// Householder steps j_start..p-1 on B and rhs, no back substitution (rhs is
+// left holding Q^T rhs): a factor from scratch (j_start = 0) that is kept for
+// later updates, or the appended block of the QR update.  Not inlined.
+template <class Team, typename T>
+__device__ __noinline__ int qr_factor_team(Team team, T *B, int q, int p, T *rhs, T *vhead, T *vtvs, T small,
+                                           int j_start) {
+    int rank_flag = 0;
+    for (int j = j_start; j < p; ++j) householder_step(team, B, q, p, rhs, vhead, vtvs, j, j + 1, small, rank_flag);
+    return rank_flag;
+}
+
+constexpr int kPanel = 16;
+
+// Compact-WY pieces shared by the panel factorization and the QR update.
+// V: nb explicit reflectors (zeros above the diagonal, heads on it) of
+// length qq in shared memory, ld qq; vtv: their v^T v.
+// T (kPanel x kPanel in tm) of H_0 ... H_{nb-1} = I - V T V^T:
+// y(s,t) = v_s^T v_t (s < t), then column by column
+// T(t,t) = tau_t, T(0:t, t) = -tau_t T(0:t, 0:t) y(0:t, t).
+template <class Team, typename T>
+__device__ __forceinline__ void wy_form_T(const Team &team, const T *V, int qq, int nb, const T *vtv, T *tm) {
+    const int me = team.rank();
+    const int lane = me & 31, wid = me >> 5;
+    constexpr int NW = (Team::SIZE + 31) / 32;
+    for (int pair = wid; pair < nb * nb; pair += NW) {
+        const int s_ = pair / nb, t_ = pair - s_ * nb;
+        if (s_ >= t_) continue;
+        const T *vs = V + (int64_t)s_ * qq, *vt = V + (int64_t)t_ * qq;
+        T d = 0;
+        for (int r = t_ + lane; r < qq; r += 32) d += vs[r] * vt[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0) tm[s_ * kPanel + t_] = d;
+    }
+    team.sync();
+    for (int t = 0; t < nb; ++t) {
+        const T vv = vtv[t];
+        const T tau = (vv > T(0)) ? T(2) / vv : T(0);
+        T val = T(0);
+        if (me < t) {
+            T acc = 0;
+            for (int s2 = me; s2 < t; ++s2) acc += tm[me * kPanel + s2] * tm[s2 * kPanel + t];
+            val = -tau * acc;
+        }
+        team.sync();
+        if (me < t) tm[me * kPanel + t] = val;
+        if (me == t) tm[t * kPanel + t] = tau;
+        team.sync();
+    }
+}
+
+// Columns c in [c_lo, c_hi] of B (ld q; c == p stands for rhs), rows
+// j0..j0+qq-1: C <- C - V (T^T (V^T C)).  Each warp takes kCols columns at a
+// time so that every reflector value read from shared memory serves kCols
+// columns.  Ends with a team synchronisation.
+template <class Team, typename T>
+__device__ __forceinline__ void wy_apply(const Team &team, const T *V, int qq, int nb, const T *tm, T *B, int q,
+                                         int p, T *rhs, int j0, int c_lo, int c_hi) {
+    const int me = team.rank();
+    const int lane = me & 31, wid = me >> 5;
+    constexpr int NW = (Team::SIZE + 31) / 32;
+    constexpr int kCols = 4;
+    for (int c0 = c_lo + wid * kCols; c0 <= c_hi; c0 += NW * kCols) {
+        T *tc[kCols];
+#pragma unroll
+        for (int x = 0; x < kCols; ++x) {
+            const int c = c0 + x;
+            tc[x] = (c > c_hi) ? nullptr : ((c < p) ? B + (int64_t)c * q + j0 : rhs + j0);
+        }
+        T wv[kCols][kPanel];
+#pragma unroll
+        for (int x = 0; x < kCols; ++x)
+#pragma unroll
+            for (int u = 0; u < kPanel; ++u) wv[x][u] = T(0);
+        for (int r = lane; r < qq; r += 32) {
+            T cr[kCols];
+#pragma unroll
+            for (int x = 0; x < kCols; ++x) cr[x] = tc[x] ? tc[x][r] : T(0);
+#pragma unroll
+            for (int u = 0; u < kPanel; ++u) {
+                if (u < nb) {
+                    const T v = V[(int64_t)u * qq + r];
+#pragma unroll
+                    for (int x = 0; x < kCols; ++x) wv[x][u] += v * cr[x];
+                }
+            }
+        }
+#pragma unroll
+        for (int x = 0; x < kCols; ++x)
+#pragma unroll
+            for (int u = 0; u < kPanel; ++u)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) wv[x][u] += __shfl_xor_sync(0xffffffffu, wv[x][u], o);
+        // w2 = T^T w (kept in wv, highest u first so that lower entries are still w)
+#pragma unroll
+        for (int x = 0; x < kCols; ++x) {
+#pragma unroll
+            for (int u = kPanel - 1; u >= 0; --u) {
+                T acc = 0;
+#pragma unroll
+                for (int s2 = 0; s2 <= u; ++s2)
+                    if (u < nb) acc += tm[s2 * kPanel + u] * wv[x][s2];
+                wv[x][u] = acc;
+            }
+        }
+        for (int r = lane; r < qq; r += 32) {
+            T acc[kCols];
+#pragma unroll
+            for (int x = 0; x < kCols; ++x) acc[x] = tc[x] ? tc[x][r] : T(0);
+#pragma unroll
+            for (int u = 0; u < kPanel; ++u) {
+                if (u < nb) {
+                    const T v = V[(int64_t)u * qq + r];
+#pragma unroll
+                    for (int x = 0; x < kCols; ++x) acc[x] -= v * wv[x][u];
+                }
+            }
+#pragma unroll
+            for (int x = 0; x < kCols; ++x)
+                if (tc[x]) tc[x][r] = acc[x];
+        }
+    }
+    team.sync();
+}
+
 // Blocked Householder QR (compact WY) for the bins whose workspace is in
 // global memory.  Panels of nb <= kPanel columns (nb chosen so that rows j0..q
 // of the panel fit the shared-memory staging area) are copied to shared
@@ -207,15 +347,17 @@ __device__ __noinline__ int qr_solve_team(Team team, T *B, int q, int p, T *rhs,
 // (zeros above the head, v(j) on the diagonal); with T upper triangular,
 // H_1...H_nb = I - V T V^T, every trailing column and the right-hand side get
 //   C <- C - V (T^T (V^T C))
-// in one pass (one warp per column), so the trailing matrix in global memory
+// in one pass (one warp per four columns), so the trailing matrix in global memory
 // is streamed once per panel instead of once per reflector.  A panel that does
 // not fit four columns falls back to single Householder steps.  The
 // reflectors, R and rhs are those of the unblocked version up to rounding.
-constexpr int kPanel = 16;
-
+// j_start > 0 factors only columns j_start..p-1 (the columns appended to a
+// factor whose first j_start columns are done, Section 3); backsub = false
+// leaves Q^T rhs in rhs.
 template <class Team, typename T>
 __device__ __noinline__ int qr_solve_staged(Team team, T *B, int q, int p, T *rhs, T *vhead, T *vtvs, T small,
-                                            T *stage, int stage_bytes) {
+                                            T *stage, int stage_bytes,
+                                            int j_start = 0, bool backsub = true) {
     const int me = team.rank();
     const int lane = me & 31, wid = me >> 5;
     constexpr int NW = (Team::SIZE + 31) / 32;
@@ -223,7 +365,7 @@ __device__ __noinline__ int qr_solve_staged(Team team, T *B, int q, int p, T *rh
     T *V = stage + kPanel * kPanel;    // panel, ld = q - j0
     const int64_t velems = (int64_t)stage_bytes / (int64_t)sizeof(T) - kPanel * kPanel;
     int rank_flag = 0;
-    int j0 = 0;
+    int j0 = j_start;
     while (j0 < p) {
         const int qq = q - j0;
         int nb = (int)min((int64_t)kPanel, velems / (int64_t)max(qq, 1));
@@ -284,101 +426,12 @@ __device__ __noinline__ int qr_solve_staged(Team team, T *B, int q, int p, T *rh
         }
         for (int e = me; e < kPanel * kPanel; e += Team::SIZE) tm[e] = T(0);
         team.sync();
-        // 5. T: y(s,t) = v_s^T v_t (s < t), then column by column
-        //    T(t,t) = tau_t, T(0:t, t) = -tau_t T(0:t, 0:t) y(0:t, t)
-        for (int pair = wid; pair < nb * nb; pair += NW) {
-            const int s_ = pair / nb, t_ = pair - s_ * nb;
-            if (s_ >= t_) continue;
-            const T *vs = V + (int64_t)s_ * qq, *vt = V + (int64_t)t_ * qq;
-            T d = 0;
-            for (int r = t_ + lane; r < qq; r += 32) d += vs[r] * vt[r];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-            if (lane == 0) tm[s_ * kPanel + t_] = d;
-        }
-        team.sync();
-        for (int t = 0; t < nb; ++t) {
-            const T vv = vtvs[j0 + t];
-            const T tau = (vv > T(0)) ? T(2) / vv : T(0);
-            T val = T(0);
-            if (me < t) {
-                T acc = 0;
-                for (int s2 = me; s2 < t; ++s2) acc += tm[me * kPanel + s2] * tm[s2 * kPanel + t];
-                val = -tau * acc;
-            }
-            team.sync();
-            if (me < t) tm[me * kPanel + t] = val;
-            if (me == t) tm[t * kPanel + t] = tau;
-            team.sync();
-        }
-        // 6. trailing columns and rhs: C <- C - V (T^T (V^T C)), rows j0..q-1;
-        //    each warp takes kCols columns at a time so that every reflector
-        //    value read from shared memory serves kCols columns
-        constexpr int kCols = 4;
-        for (int c0 = j0 + nb + wid * kCols; c0 <= p; c0 += NW * kCols) {
-            T *tc[kCols];
-#pragma unroll
-            for (int x = 0; x < kCols; ++x) {
-                const int c = c0 + x;
-                tc[x] = (c < p) ? B + (int64_t)c * q + j0 : ((c == p) ? rhs + j0 : nullptr);
-            }
-            T wv[kCols][kPanel];
-#pragma unroll
-            for (int x = 0; x < kCols; ++x)
-#pragma unroll
-                for (int u = 0; u < kPanel; ++u) wv[x][u] = T(0);
-            for (int r = lane; r < qq; r += 32) {
-                T cr[kCols];
-#pragma unroll
-                for (int x = 0; x < kCols; ++x) cr[x] = tc[x] ? tc[x][r] : T(0);
-#pragma unroll
-                for (int u = 0; u < kPanel; ++u) {
-                    if (u < nb) {
-                        const T v = V[(int64_t)u * qq + r];
-#pragma unroll
-                        for (int x = 0; x < kCols; ++x) wv[x][u] += v * cr[x];
-                    }
-                }
-            }
-#pragma unroll
-            for (int x = 0; x < kCols; ++x)
-#pragma unroll
-                for (int u = 0; u < kPanel; ++u)
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) wv[x][u] += __shfl_xor_sync(0xffffffffu, wv[x][u], o);
-            // w2 = T^T w (kept in wv, highest u first so that lower entries are still w)
-#pragma unroll
-            for (int x = 0; x < kCols; ++x) {
-#pragma unroll
-                for (int u = kPanel - 1; u >= 0; --u) {
-                    T acc = 0;
-#pragma unroll
-                    for (int s2 = 0; s2 <= u; ++s2)
-                        if (u < nb) acc += tm[s2 * kPanel + u] * wv[x][s2];
-                    wv[x][u] = acc;
-                }
-            }
-            for (int r = lane; r < qq; r += 32) {
-                T acc[kCols];
-#pragma unroll
-                for (int x = 0; x < kCols; ++x) acc[x] = tc[x] ? tc[x][r] : T(0);
-#pragma unroll
-                for (int u = 0; u < kPanel; ++u) {
-                    if (u < nb) {
-                        const T v = V[(int64_t)u * qq + r];
-#pragma unroll
-                        for (int x = 0; x < kCols; ++x) acc[x] -= v * wv[x][u];
-                    }
-                }
-#pragma unroll
-                for (int x = 0; x < kCols; ++x)
-                    if (tc[x]) tc[x][r] = acc[x];
-            }
-        }
-        team.sync();
+        // 5. T, 6. trailing columns and rhs, rows j0..q-1
+        wy_form_T(team, V, qq, nb, vtvs + j0, tm);
+        wy_apply(team, V, qq, nb, tm, B, q, p, rhs, j0, j0 + nb, p);
         j0 += nb;
     }
-    back_substitute_team(team, B, q, p, rhs, small);
+    if (backsub) back_substitute_team(team, B, q, p, rhs, small);
     return rank_flag;
 }
 
@@ -404,6 +457,57 @@ __device__ __noinline__ void apply_qt_team(Team team, const T *B, int q, int p, 
     back_substitute_team(team, B, q, p, rhs, small);
 }
 
+// The QR update of Section 3, first half: the reflectors 0..p0-1 of a
+// finished factor (built on q0 rows; every row below is zero in them) applied
+// to the appended columns p0..p-1 of B (ld q), rows j..q0-1.  With a staging
+// area, panels of up to kPanel old reflectors are copied to shared memory as
+// explicit V and applied in compact-WY form; otherwise (or when a panel does
+// not fit four reflectors) one reflector per pass, one warp per column.
+template <class Team, typename T>
+__device__ __noinline__ void qr_update_apply(Team team, T *B, int q, int p, int q0, int p0, const T *vhead,
+                                             const T *vtvs, T *stage, int stage_bytes) {
+    const int me = team.rank();
+    const int lane = me & 31, wid = me >> 5;
+    constexpr int NW = (Team::SIZE + 31) / 32;
+    T *tm = stage;
+    T *V = stage + kPanel * kPanel;
+    const int64_t velems = stage_bytes > 0 ? (int64_t)stage_bytes / (int64_t)sizeof(T) - kPanel * kPanel : 0;
+    int j0 = 0;
+    while (j0 < p0) {
+        const int qq = q0 - j0;
+        int nb = (int)min((int64_t)kPanel, velems / (int64_t)max(qq, 1));
+        nb = min(nb, p0 - j0);
+        if (nb < 4) {
+            const T *col = B + (int64_t)j0 * q;
+            const T v0 = vhead[j0], vtv = vtvs[j0];
+            if (vtv > T(0)) {
+                const T two_over = T(2) / vtv;
+                for (int c = p0 + wid; c < p; c += NW) {
+                    T *t = B + (int64_t)c * q;
+                    T d = 0;
+                    for (int i = j0 + lane; i < q0; i += 32) d += ((i == j0) ? v0 : col[i]) * t[i];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                    const T f = d * two_over;
+                    for (int i = j0 + lane; i < q0; i += 32) t[i] -= f * ((i == j0) ? v0 : col[i]);
+                }
+            }
+            team.sync();
+            ++j0;
+            continue;
+        }
+        for (int idx = me; idx < nb * qq; idx += Team::SIZE) {
+            const int t = idx / qq, r = idx - t * qq;
+            V[idx] = (r < t) ? T(0) : ((r == t) ? vhead[j0 + t] : B[(int64_t)(j0 + t) * q + j0 + r]);
+        }
+        for (int e = me; e < kPanel * kPanel; e += Team::SIZE) tm[e] = T(0);
+        team.sync();
+        wy_form_T(team, V, qq, nb, vtvs + j0, tm);
+        wy_apply(team, V, qq, nb, tm, B, q, p, (T *)nullptr, j0, p0, p - 1);
+        j0 += nb;
+    }
+}
+
 template <class Team, typename T> struct Column {
     const Team &team;
     const DevA &A;
@@ -416,6 +520,8 @@ template <class Team, typename T> struct Column {
     int rank_flag;
     double rho;
     T small_last;  // rank threshold of the last solve (reused by the adjoint)
+    T fro2_f;      // ||B||_F^2 of the kept factor (Caps::append)
+    bool fact_valid;  // B, vhead, vtv, qte, Ip, Jp hold the factor of the current J (Caps::append)
     // per-column work counters (integers; committed only when the column finishes)
     long long c_qr, c_res, c_ref, c_ref64, c_bytes;
     int c_solves, c_drops, c_pmax, c_qmax;
@@ -500,13 +606,38 @@ template <class Team, typename T> struct Column {
             }
         }
         if constexpr (!std::is_same<Team, WarpTeam>::value) {
-            if (cap.stage_bytes > 0 && p >= 2 * kPanel) {
+            const bool keep = cap.append != 0;  // keep Q^T e_k for later updates
+            if (cap.stage_bytes > 0 && p >= 2 * kPanel)
                 rank_flag = qr_solve_staged<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.vtv, small, (T *)w.stage,
-                                                     cap.stage_bytes);
-                return;
+                                                     cap.stage_bytes, 0, !keep);
+            else
+                rank_flag = keep ? qr_factor_team<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.vtv, small, 0)
+                                 : qr_solve_team<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.vtv, small);
+            if (keep) {
+                // a factor from scratch: factor order = sorted order
+                const int me = team.rank();
+                for (int i = me; i < q; i += Team::SIZE) {
+                    w.qte[i] = w.rhs[i];
+                    w.Ip[i] = i;
+                }
+                for (int c = me; c < p; c += Team::SIZE) w.Jp[c] = c;
+                team.sync();
+                back_substitute_team(team, w.B, q, p, w.rhs, small);
+                fact_valid = true;
             }
+            return;
         }
         rank_flag = qr_solve_team<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.vtv, small);
+    }
+
+    // factor row of sorted I position i / factor column of sorted J position c
+    __device__ __forceinline__ int frow(int i) const {
+        if constexpr (std::is_same<Team, WarpTeam>::value) return i;
+        else return cap.append ? w.Ip[i] : i;
+    }
+    __device__ __forceinline__ int fcol(int c) const {
+        if constexpr (std::is_same<Team, WarpTeam>::value) return c;
+        else return cap.append ? w.Jp[c] : c;
     }
 
     // rhs <- R^{-1} Q^T rhs with the stored reflectors
@@ -566,10 +697,51 @@ template <class Team, typename T> struct Column {
         team.sync();
     }
 
-    // Solve the LS problem on the current J (Eq. 2.3).  `append`: J extends the
-    // previously solved J (the paper's QR update; counted as such).
+    // One step of refinement (FP32_REFINE): r = B m - e in double,
+    // m += R^{-1} Q^T (-r) with the factor of the last solve.
+    __device__ __forceinline__ void refine_step(T small) {
+        const int me = team.rank();
+        residual(true);
+        int pk = lower_bound_i32(w.I, q, k);
+        bool has_k = pk < q && w.I[pk] == k;
+        for (int i = me; i < q; i += Team::SIZE) {
+            int si = (has_k || i < pk) ? i : i + 1;
+            w.rhs[frow(i)] = (T)(-w.r[si]);
+        }
+        team.sync();
+        apply_qt_solve(small);
+        for (int c = me; c < p; c += Team::SIZE) w.m[c] += (double)w.rhs[fcol(c)];
+        team.sync();
+        c_ref += 4LL * q * p + (long long)p * p;
+    }
+
+    __device__ __forceinline__ void count_solve(bool append) {
+        c_qr += append ? solve_flops(q0, p0, q, p) : solve_flops(0, 0, q, p);
+        q0 = q;
+        p0 = p;
+        c_solves += 1;
+        c_pmax = max(c_pmax, p);
+        c_qmax = max(c_qmax, q);
+    }
+
+    // Solve the LS problem on the current J (Eq. 2.3).  `append`: J extends
+    // the previously solved J by Jhat (the paper's QR update; counted as
+    // such).  The CTA bins (Caps::append) then update the kept factor instead
+    // of refactoring when the last solve left one.
     __device__ bool solve(bool append) {
         const int me = team.rank();
+        if constexpr (!std::is_same<Team, WarpTeam>::value) {
+            if (cap.append && append && fact_valid) {
+                const int st = update_factor();
+                if (st == 0) return false;
+                if (st > 0) {
+                    if (P.precision == RSAI_FP32_REFINE) refine_step(small_last);
+                    count_solve(append);
+                    return true;
+                }
+            }
+            fact_valid = false;
+        }
         build_jhash();
         if (!rows_of_J()) return false;
         if ((int64_t)q * p > cap.bcap) return false;
@@ -628,7 +800,9 @@ template <class Team, typename T> struct Column {
                 }
             }
         }
-        T fro = sqrt(team.sum(fro2));
+        const T fro2s = team.sum(fro2);
+        if constexpr (!std::is_same<Team, WarpTeam>::value) fro2_f = fro2s;
+        T fro = sqrt(fro2s);
         team.sync();
         const T small = T(q) * T(2.0 * Unit<T>::u) * fro;
         small_last = small;
@@ -641,29 +815,125 @@ template <class Team, typename T> struct Column {
             qr_solve(small);
             for (int c = me; c < p; c += Team::SIZE) w.m[c] = (double)w.rhs[c];
             team.sync();
-            if (P.precision == RSAI_FP32_REFINE) {
-                // one step of refinement: r = B m - e in double, m += R^{-1} Q^T (-r)
-                residual(true);
-                int pk = lower_bound_i32(w.I, q, k);
-                bool has_k = pk < q && w.I[pk] == k;
-                for (int i = me; i < q; i += Team::SIZE) {
-                    int si = (has_k || i < pk) ? i : i + 1;
-                    w.rhs[i] = (T)(-w.r[si]);
+            if (P.precision == RSAI_FP32_REFINE) refine_step(small);
+        }
+        count_solve(append);
+        return true;
+    }
+
+    // The QR update of Section 3 (CTA bins).  J grew by Jhat (sorted, in
+    // w.buf[0..p - p0)) since the last solve, whose factor is kept in factor
+    // order: the rows and columns of earlier solves first, in the order in
+    // which they entered, the new ones after them (w.Ip / w.Jp give the factor
+    // position of each sorted I / J entry, w.qte holds Q^T e_k).  The new rows
+    // of I are zero in the old columns, so the old reflectors act on the
+    // appended columns only (qr_update_apply); the appended block is then
+    // factored below row p0.  Returns 1 when m holds the solution, 0 on
+    // overflow, -1 when the caller has to solve from scratch (q < p).
+    __device__ int update_factor() {
+        const int me = team.rank();
+        const int qo = (int)q0, po = (int)p0, nj = p - po;
+        fact_valid = false;
+        // Jhat and the old sorted I are kept (rows_of_J reuses buf; the
+        // residual rewrites S afterwards)
+        for (int b = me; b < nj; b += Team::SIZE) w.Jn[b] = w.buf[b];
+        for (int i = me; i < qo; i += Team::SIZE) w.S[i] = w.I[i];
+        team.sync();
+        build_jhash();
+        if (!rows_of_J()) return 0;
+        if ((int64_t)q * p > cap.bcap) return 0;
+        if (q < p || q > cap.scap || p > cap.scap) return -1;
+        // factor rows: old rows keep theirs, new rows follow in ascending order
+        int32_t *ipn = w.buf2, *jpn = w.buf;
+        int base = 0;
+        for (int i0 = 0; i0 < q; i0 += Team::SIZE) {
+            const int i = i0 + me;
+            const int io = (i < q) ? find_i32(w.S, qo, w.I[i]) : 0;
+            const int fnew = (i < q) && (io < 0);
+            int tot;
+            const int pos = team.scan(fnew, &tot);
+            if (i < q) ipn[i] = fnew ? qo + base + pos : w.Ip[io];
+            base += tot;
+        }
+        // factor columns: the old ones keep theirs, Jhat follows in ascending
+        // order (an old column is the (c - b)-th of the old sorted J when b
+        // entries of Jhat precede it)
+        for (int c = me; c < p; c += Team::SIZE) {
+            const int b = lower_bound_i32(w.Jn, nj, w.J[c]);
+            jpn[c] = (b < nj && w.Jn[b] == w.J[c]) ? po + b : w.Jp[min(max(c - b, 0), po - 1)];
+        }
+        team.sync();
+        for (int i = me; i < q; i += Team::SIZE) w.Ip[i] = ipn[i];
+        for (int c = me; c < p; c += Team::SIZE) w.Jp[c] = jpn[c];
+        // B: leading dimension q0 -> q in place (column 0 stays).  Old flat
+        // index o moves to (o / q0) q + o % q0 >= o, so chunks taken from the
+        // top down, each read into registers before any of it is written,
+        // never overwrite an entry that is still to be read.
+        if (q > qo) {
+            constexpr int K = 8;
+            constexpr int64_t chunk = (int64_t)K * Team::SIZE;
+            for (int64_t hi = (int64_t)qo * po; hi > qo; hi -= chunk) {
+                const int64_t lo = max((int64_t)qo, hi - chunk);
+                T v[K];
+#pragma unroll
+                for (int u = 0; u < K; ++u) {
+                    const int64_t o = lo + me + (int64_t)u * Team::SIZE;
+                    v[u] = (o < hi) ? w.B[o] : T(0);
                 }
                 team.sync();
-                apply_qt_solve(small);
-                for (int c = me; c < p; c += Team::SIZE) w.m[c] += (double)w.rhs[c];
-                team.sync();
-                c_ref += 4LL * q * p + (long long)p * p;
+#pragma unroll
+                for (int u = 0; u < K; ++u) {
+                    const int64_t o = lo + me + (int64_t)u * Team::SIZE;
+                    if (o < hi) w.B[(o / qo) * q + o % qo] = v[u];
+                }
+            }
+            team.sync();
+            const int nr = q - qo;
+            for (int64_t idx = me; idx < (int64_t)po * nr; idx += Team::SIZE) {
+                const int c = (int)(idx / nr);
+                w.B[(int64_t)c * q + qo + (idx - (int64_t)c * nr)] = T(0);
             }
         }
-        c_qr += append ? solve_flops(q0, p0, q, p) : solve_flops(0, 0, q, p);
-        q0 = q;
-        p0 = p;
-        c_solves += 1;
-        c_pmax = max(c_pmax, p);
-        c_qmax = max(c_qmax, q);
-        return true;
+        for (int64_t idx = (int64_t)po * q + me; idx < (int64_t)p * q; idx += Team::SIZE) w.B[idx] = T(0);
+        for (int f = qo + me; f < q; f += Team::SIZE) w.qte[f] = T(0);
+        team.sync();
+        // the appended columns, placed by the factor row of each entry
+        T fro2 = 0;
+        for (int b = me; b < nj; b += Team::SIZE) {
+            const int32_t j = w.Jn[b];
+            T *Bc = w.B + (int64_t)(po + b) * q;
+            for (int64_t e = A.col_ptr[j]; e < A.col_ptr[j + 1]; ++e) {
+                const T a = (T)A.cval[e];
+                const int ii = find_i32(w.I, q, A.row_idx[e]);
+                if (ii >= 0) Bc[w.Ip[ii]] = a;
+                fro2 += a * a;
+            }
+        }
+        fro2_f += team.sum(fro2);
+        const T small = T(q) * T(2.0 * Unit<T>::u) * sqrt(fro2_f);
+        small_last = small;
+        // e_k on the new rows: k enters I late when a drop had removed it
+        if (me == 0) {
+            const int ik = lower_bound_i32(w.I, q, k);
+            if (ik < q && w.I[ik] == k && w.Ip[ik] >= qo) w.qte[w.Ip[ik]] = T(1);
+        }
+        team.sync();
+        qr_update_apply<Team, T>(team, w.B, q, p, qo, po, w.vhead, w.vtv, (T *)w.stage, cap.stage_bytes);
+        if (cap.stage_bytes > 0 && p >= 2 * kPanel)
+            qr_solve_staged<Team, T>(team, w.B, q, p, w.qte, w.vhead, w.vtv, small, (T *)w.stage, cap.stage_bytes,
+                                     po, false);
+        else
+            qr_factor_team<Team, T>(team, w.B, q, p, w.qte, w.vhead, w.vtv, small, po);
+        int rf = 0;
+        for (int j = me; j < p; j += Team::SIZE) rf |= (fabs(w.B[(int64_t)j * q + j]) <= small) ? 1 : 0;
+        rank_flag = team.sum(rf) > 0 ? 1 : 0;
+        for (int j = me; j < p; j += Team::SIZE) w.rhs[j] = w.qte[j];
+        team.sync();
+        back_substitute_team(team, w.B, q, p, w.rhs, small);
+        for (int c = me; c < p; c += Team::SIZE) w.m[c] = (double)w.rhs[w.Jp[c]];
+        team.sync();
+        fact_valid = true;
+        return 1;
     }
 
     // Eq. 4.3: drop |m_j| <= tau, keep at least the largest, re-solve once.
@@ -872,6 +1142,7 @@ template <class Team, typename T> struct Column {
     // J = Jk (sorted, length pk): false if it does not fit this bin
     __device__ bool load_pattern(const int32_t *Jk, int pk) {
         p = pk; q = 0; s = 0; nR = 0; l = 0; q0 = 0; p0 = 0; rank_flag = 0; rho = 0.0;
+        if constexpr (!std::is_same<Team, WarpTeam>::value) fact_valid = false;
         c_qr = c_res = c_ref = c_ref64 = c_bytes = 0;
         c_solves = c_drops = c_pmax = c_qmax = 0;
         if (pk > cap.pcap || pk < 1) return false;
@@ -1017,6 +1288,7 @@ template <class Team, typename T> struct Column {
     __device__ int run() {
         const int me = team.rank();
         p = 1; q = 0; s = 0; nR = 0; l = 0; q0 = 0; p0 = 0; rank_flag = 0; rho = 0.0;
+        if constexpr (!std::is_same<Team, WarpTeam>::value) fact_valid = false;
         c_qr = c_res = c_ref = c_ref64 = c_bytes = 0;
         c_solves = c_drops = c_pmax = c_qmax = 0;
         if (me == 0) w.J[0] = k;

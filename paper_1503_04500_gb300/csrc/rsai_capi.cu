@@ -243,7 +243,7 @@ int plan_bins(rsai_handle *h) {
     if (h->tuning.warp_bin_ctas_per_sm > 0) occ = std::min(occ, h->tuning.warp_bin_ctas_per_sm);
     h->grid_w = h->sms * occ;
     // bin C: shared-memory workspace as large as the opt-in limit allows
-    Caps c{1024, 256, 4096, std::min(rneed * 2, 2048), 0, 0, 0, 0};
+    Caps c{1024, 256, 4096, std::min(rneed * 2, 2048), 0, 0, 0, 0, 1};
     size_t base = fp32 ? work_bytes<float>(c) : work_bytes<double>(c);
     size_t avail = (size_t)max_optin - 2048;
     if (base >= avail) return RSAI_ERR_CUDA;
@@ -253,7 +253,7 @@ int plan_bins(rsai_handle *h) {
     if (occ < 1) return RSAI_ERR_CUDA;
     h->grid_c = h->sms * occ;
     // bin G: a global-memory slab per CTA, one CTA per SM
-    h->capG = Caps{32768, 4096, 131072, 8192, (int64_t)1 << 24, 0, 0, max_optin - 2048};
+    h->capG = Caps{32768, 4096, 131072, 8192, (int64_t)1 << 24, 0, 0, max_optin - 2048, 1};
     h->gstride = ((fp32 ? work_bytes<float>(h->capG) : work_bytes<double>(h->capG)) + 255) & ~size_t(255);
     h->grid_g = 1;  // sized by the first build (size_global_slab)
     return RSAI_OK;
