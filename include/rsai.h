@@ -31,6 +31,7 @@
 #ifndef RSAI_H
 #define RSAI_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -312,6 +313,32 @@ rsai_status rsai_set_tuning(rsai_handle *h, const rsai_tuning *t);
 
 /* Release a handle and its device memory (NULL is a no-op). */
 void rsai_handle_free(rsai_handle *h);
+
+/*
+ * rsai_set_allocator -- where the library takes its device memory from.
+ *
+ * No counterpart in the paper: the plumbing that lets a host framework (for
+ * example PyTorch's caching allocator) own every device buffer of the library,
+ * as the survey of the interface asks (workspace through an optional
+ * allocator callback).
+ *
+ * alloc(bytes, stream, ctx) returns a device pointer (aligned to at least 256
+ * bytes) usable in stream order on `stream`, or NULL when out of memory (the
+ * call then fails with RSAI_ERR_OOM).  release(ptr, bytes, stream, ctx) gives
+ * a buffer back; `stream` is the stream its last use was ordered on, or NULL
+ * after a device-wide synchronisation (rsai_handle_free).  Both are called on
+ * the calling host thread, never during a CUDA graph replay.
+ *
+ * The setting is process-wide and applies to handles created afterwards (a
+ * handle frees with the allocator it was created with), to the temporaries of
+ * rsai_refit and to the workspace of rsai_bicgstab.  alloc = release = NULL
+ * restores cudaMallocAsync / cudaFreeAsync.  Not thread-safe against builds
+ * running on other threads.  Errors: INVALID_ARG when exactly one of the two
+ * is NULL.
+ */
+typedef void *(*rsai_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*rsai_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+rsai_status rsai_set_allocator(rsai_alloc_fn alloc, rsai_free_fn release, void *ctx);
 
 /*
  * rsai_peak_fma -- measure the CUDA-core FMA pipe rate: launches a grid of

@@ -134,12 +134,17 @@ namespace rsai {
 
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+size_t bicgstab_workspace_bytes(int64_t n) {
+    return sizeof(double) * (size_t)(n > 0 ? n : 1) * 9 + sizeof(double) * (kDotBlocks + 16);
+}
+
 int bicgstab_run(int64_t n, const int64_t *Arp, const int32_t *Aci, const double *Av, const int64_t *Mrp,
                  const int32_t *Mci, const double *Mv, const double *b, double *x, double rtol, int maxit,
-                 int *iters, double *relres, cudaStream_t st) {
+                 int *iters, double *relres, cudaStream_t st, double *work) {
     const size_t vb = sizeof(double) * (size_t)(n > 0 ? n : 1);
-    double *buf = nullptr;
-    if (cudaMallocAsync((void **)&buf, vb * 9 + sizeof(double) * (kDotBlocks + 16), st) != cudaSuccess)
+    double *buf = work;
+    const bool own = work == nullptr;  // else the caller's workspace of bicgstab_workspace_bytes(n)
+    if (own && cudaMallocAsync((void **)&buf, bicgstab_workspace_bytes(n), st) != cudaSuccess)
         return RSAI_ERR_OOM;
     double *r = buf, *rhat = r + n, *p = rhat + n, *v = p + n, *s = v + n, *t = s + n, *y = t + n, *tmp = y + n,
            *tmp2 = tmp + n, *partials = tmp2 + n, *sc = partials + kDotBlocks;
@@ -159,13 +164,13 @@ int bicgstab_run(int64_t n, const int64_t *Arp, const int32_t *Aci, const double
     };
     k_bicg_init<<<blocks_for(n, T), T, 0, st>>>(n, b, r, rhat, p, v, y, sc);
     launch_dot(n, b, b, partials, sc + 9, st);
-    if (!fetch(10)) { cudaFreeAsync(buf, st); return RSAI_ERR_CUDA; }
+    if (!fetch(10)) { if (own) cudaFreeAsync(buf, st); return RSAI_ERR_CUDA; }
     const double nb = sqrt(h[9]);
     if (nb == 0.0) {
         cudaMemsetAsync(x, 0, vb, st);
         *iters = 0;
         *relres = 0.0;
-        cudaFreeAsync(buf, st);
+        if (own) cudaFreeAsync(buf, st);
         return RSAI_OK;
     }
     for (it = 1; it <= maxit; ++it) {
@@ -205,7 +210,7 @@ int bicgstab_run(int64_t n, const int64_t *Arp, const int32_t *Aci, const double
     launch_dot(n, tmp2, tmp2, partials, sc + 10, st);
     double rr = 0.0;
     cudaMemcpyAsync(&rr, sc + 10, sizeof(double), cudaMemcpyDeviceToHost, st);
-    cudaFreeAsync(buf, st);
+    if (own) cudaFreeAsync(buf, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return RSAI_ERR_CUDA;
     *iters = it;
     *relres = sqrt(rr) / nb;

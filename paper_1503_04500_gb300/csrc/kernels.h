@@ -62,7 +62,9 @@ cudaError_t launch_spmv(int64_t n, const int64_t *row_ptr, const int32_t *col_id
 cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *partials, double *out, cudaStream_t st);
 int bicgstab_run(int64_t n, const int64_t *Arp, const int32_t *Aci, const double *Av, const int64_t *Mrp,
                  const int32_t *Mci, const double *Mv, const double *b, double *x, double rtol, int maxit,
-                 int *iters, double *relres, cudaStream_t st);
+                 int *iters, double *relres, cudaStream_t st, double *work = nullptr);
+// device bytes bicgstab_run needs as its workspace for size n
+size_t bicgstab_workspace_bytes(int64_t n);
 
 // BiCGStab vector steps (apply_kernels.cu); scalars on the device
 __global__ void k_bicg_p(int64_t n, const double *sc, const double *r, const double *v, double *p);

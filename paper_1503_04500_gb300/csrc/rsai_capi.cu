@@ -3,8 +3,9 @@
 // A handle owns: a device copy of A (CSR + CSC + the CSC->CSR position map),
 // the per-column outputs, the result pool, the overflow queues of the size
 // bins, M in CSC and CSR, and the CUDA graph of the build sequence.  All device
-// memory is taken with cudaMallocAsync on the caller's stream and released
-// with cudaFreeAsync; nothing is allocated by the build sequence itself, so
+// memory is taken on the caller's stream, from the allocator installed with
+// rsai_set_allocator when the handle was created, else with cudaMallocAsync /
+// cudaFreeAsync; nothing is allocated by the build sequence itself, so
 // rsai_rebuild can replay it as one CUDA graph.
 #include <algorithm>
 #include <cmath>
@@ -16,6 +17,16 @@
 #include "kernels.h"
 
 using namespace rsai;
+
+namespace {
+// device memory source: a caller's allocator, or the CUDA stream-ordered one
+struct Allocator {
+    rsai_alloc_fn alloc = nullptr;
+    rsai_free_fn release = nullptr;
+    void *ctx = nullptr;
+};
+Allocator g_allocator;  // process-wide; a handle keeps the one in effect when it was created
+}  // namespace
 
 struct rsai_handle {
     int device = 0;
@@ -75,7 +86,8 @@ struct rsai_handle {
     cudaGraphExec_t graph = nullptr;
     cudaStream_t graph_stream = nullptr;
     // host copy of the last statistics
-    std::vector<void *> allocs;
+    std::vector<std::pair<void *, size_t>> allocs;
+    Allocator allocator;
     cudaStream_t alloc_stream = nullptr;
 };
 
@@ -91,16 +103,40 @@ double *dword(const rsai_handle *h, int at) { return reinterpret_cast<double *>(
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? RSAI_OK : RSAI_ERR_CUDA; }
 
-template <typename P> int dalloc(rsai_handle *h, P **ptr, size_t count, cudaStream_t st) {
+void *raw_alloc(const Allocator &a, size_t bytes, cudaStream_t st) {
     void *p = nullptr;
-    size_t bytes = sizeof(P) * (count ? count : 1);
+    if (a.alloc) return a.alloc(bytes, (void *)st, a.ctx);
     if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
         cudaGetLastError();
-        return RSAI_ERR_OOM;
+        return nullptr;
     }
-    h->allocs.push_back(p);
+    return p;
+}
+
+void raw_free(const Allocator &a, void *p, size_t bytes, cudaStream_t st) {
+    if (!p) return;
+    if (a.release) a.release(p, bytes, (void *)st, a.ctx);
+    else cudaFreeAsync(p, st);
+}
+
+template <typename P> int dalloc(rsai_handle *h, P **ptr, size_t count, cudaStream_t st) {
+    size_t bytes = sizeof(P) * (count ? count : 1);
+    void *p = raw_alloc(h->allocator, bytes, st);
+    if (!p) return RSAI_ERR_OOM;
+    h->allocs.push_back({p, bytes});
     *ptr = (P *)p;
     return RSAI_OK;
+}
+
+// frees one buffer taken by dalloc (stream-ordered on st)
+void dfree(rsai_handle *h, void *p, cudaStream_t st) {
+    for (size_t i = 0; i < h->allocs.size(); ++i) {
+        if (h->allocs[i].first == p) {
+            raw_free(h->allocator, p, h->allocs[i].second, st);
+            h->allocs.erase(h->allocs.begin() + i);
+            return;
+        }
+    }
 }
 
 // copy host or device memory into a device buffer
@@ -221,7 +257,10 @@ void free_all(rsai_handle *h) {
     h->graph = nullptr;
     // the caller's stream may be gone by now: wait for the device, then free
     cudaDeviceSynchronize();
-    for (void *p : h->allocs) cudaFree(p);
+    for (auto &a : h->allocs) {
+        if (h->allocator.release) h->allocator.release(a.first, a.second, nullptr, h->allocator.ctx);
+        else cudaFree(a.first);
+    }
     h->allocs.clear();
 }
 
@@ -331,8 +370,7 @@ int size_global_slab(rsai_handle *h, cudaStream_t st) {
     if (h->tuning.global_bin_ctas > 0) want = std::min(h->tuning.global_bin_ctas, h->sms);
     if (want <= h->grid_g) return RSAI_OK;
     if (h->gwork) {
-        cudaFreeAsync(h->gwork, st);
-        h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void *)h->gwork), h->allocs.end());
+        dfree(h, h->gwork, st);
         h->gwork = nullptr;
     }
     h->grid_g = want;
@@ -411,10 +449,7 @@ int build_common(rsai_handle *h, cudaStream_t st) {
             if (r == RSAI_OK) r = dalloc(h, &h->Mcsc_to_csr, c, st);
             return r;
         };
-        auto release = [&](void *p) {
-            cudaFreeAsync(p, st);
-            h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), p), h->allocs.end());
-        };
+        auto release = [&](void *p) { dfree(h, p, st); };
         TRY(alloc_m(cap));
         TRY(cuda_status(enqueue_build(h, st, nullptr, size_global_slab)));
         int32_t *retry = nullptr;
@@ -466,6 +501,7 @@ rsai_handle *new_handle(const rsai_params *params, cudaStream_t st) {
     rsai_handle *h = new (std::nothrow) rsai_handle();
     if (!h) return nullptr;
     h->alloc_stream = st;
+    h->allocator = g_allocator;
     cudaGetDevice(&h->device);
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
     h->params = *params;
@@ -729,6 +765,12 @@ rsai_status rsai_get_columns(rsai_handle *h, double *rho, int32_t *loops, int32_
     return (rsai_status)cuda_status(cudaStreamSynchronize(st));
 }
 
+rsai_status rsai_set_allocator(rsai_alloc_fn alloc, rsai_free_fn release, void *ctx) {
+    if ((alloc == nullptr) != (release == nullptr)) return RSAI_ERR_INVALID_ARG;
+    g_allocator = Allocator{alloc, release, alloc ? ctx : nullptr};
+    return RSAI_OK;
+}
+
 rsai_status rsai_apply(rsai_handle *h, const double *x, double *y, void *stream) {
     if (!h || !x || !y) return RSAI_ERR_INVALID_ARG;
     return (rsai_status)cuda_status(
@@ -743,8 +785,18 @@ rsai_status rsai_bicgstab(const rsai_csr *A, rsai_handle *M, const double *b, do
     if (M && M->n != A->n) return RSAI_ERR_SHAPE;
     int it = 0;
     double rr = 0.0;
+    const cudaStream_t st = (cudaStream_t)stream;
+    // the workspace comes from the installed allocator when there is one
+    const Allocator a = g_allocator;
+    double *work = nullptr;
+    const size_t wb = bicgstab_workspace_bytes(A->n);
+    if (a.alloc) {
+        work = (double *)raw_alloc(a, wb, st);
+        if (!work) return RSAI_ERR_OOM;
+    }
     rc = bicgstab_run(A->n, A->row_ptr, A->col_idx, A->val, M ? M->Mrowptr : nullptr, M ? M->Mcols : nullptr,
-                      M ? M->Mvals : nullptr, b, x, rtol, maxit, &it, &rr, (cudaStream_t)stream);
+                      M ? M->Mvals : nullptr, b, x, rtol, maxit, &it, &rr, st, work);
+    if (work) raw_free(a, work, wb, st);
     *iters = it;
     *relres = rr;
     return (rsai_status)rc;
@@ -799,9 +851,10 @@ rsai_status rsai_refit(rsai_handle *h, const double *A_val, double *M_val, doubl
     if (rc != RSAI_OK) return (rsai_status)rc;
     double *mv = M_val, *r2 = rho2;
     double *tmp = nullptr;
+    const size_t tmp_bytes = sizeof(double) * (size_t)(nnzM + h->n + 1);
     if (!mv || !r2) {  // outputs the caller skipped go to a temporary
-        if (cudaMallocAsync((void **)&tmp, sizeof(double) * (size_t)(nnzM + h->n + 1), st) != cudaSuccess)
-            return RSAI_ERR_OOM;
+        tmp = (double *)raw_alloc(h->allocator, tmp_bytes, st);
+        if (!tmp) return RSAI_ERR_OOM;
         if (!mv) mv = tmp;
         if (!r2) r2 = tmp + nnzM;
     }
@@ -813,7 +866,7 @@ rsai_status rsai_refit(rsai_handle *h, const double *A_val, double *M_val, doubl
     F.rho2 = r2;
     cudaMemsetAsync(h->err, 0, sizeof(int32_t), st);
     cudaError_t e = enqueue_bins(h, MODE_REFIT, A, F, h->fctr, st);
-    if (tmp) cudaFreeAsync(tmp, st);
+    if (tmp) raw_free(h->allocator, tmp, tmp_bytes, st);
     if (e != cudaSuccess) return RSAI_ERR_CUDA;
     return (rsai_status)finish_frozen(h, st);
 }
@@ -899,8 +952,7 @@ rsai_status rsai_set_tuning(rsai_handle *h, const rsai_tuning *t) {
         const int want = std::min(t->global_bin_ctas, h->sms);
         if (want > h->grid_g) {
             if (h->gwork) {
-                cudaFreeAsync(h->gwork, st);
-                h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void *)h->gwork), h->allocs.end());
+                dfree(h, h->gwork, st);
                 h->gwork = nullptr;
             }
             int rc = dalloc(h, &h->gwork, h->gstride * (size_t)want, st);

@@ -33,6 +33,7 @@ EXPORTS = [
     "rsai_rebuild", "rsai_set_values", "rsai_get_stats", "rsai_get_M", "rsai_get_columns", "rsai_refit",
     "rsai_apply", "rsai_backward", "rsai_bicgstab", "rsai_handle_free", "rsai_peak_fma", "rsai_build_phase_times",
     "rsai_bicgstab_noalloc", "rsai_build_batch", "rsai_get_block_stats", "rsai_get_tuning", "rsai_set_tuning",
+    "rsai_set_allocator",
 ]
 
 
@@ -84,7 +85,12 @@ class Stats(ctypes.Structure):
         return d
 
 
+# device allocator callbacks (rsai_alloc_fn / rsai_free_fn)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
 _lib = None
+_allocators = []  # every callback pair ever installed (handles keep calling theirs until freed)
 
 
 def load(build_if_missing: bool = False):
@@ -128,6 +134,7 @@ def load(build_if_missing: bool = False):
         "rsai_set_tuning": (i32, [vp, ctypes.POINTER(Tuning)]),
         "rsai_bicgstab_noalloc": (i32, [ctypes.POINTER(CSR), ctypes.POINTER(CSR), vp, vp, f64, i32,
                                         ctypes.POINTER(i32), ctypes.POINTER(f64), vp]),
+        "rsai_set_allocator": (i32, [ALLOC_FN, FREE_FN, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -135,6 +142,36 @@ def load(build_if_missing: bool = False):
         f.argtypes = args
     _lib = lib
     return lib
+
+
+def use_torch_allocator() -> None:
+    """Take the library's device memory from PyTorch's caching allocator.
+
+    Applies to handles created afterwards (each handle frees with the
+    allocator it was created with), to refit temporaries and to the BiCGStab
+    workspace.  The callbacks run on the calling thread, outside any graph
+    replay.
+    """
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), int(stream or 0))
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    cbs = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _allocators.append(cbs)
+    _check(load().rsai_set_allocator(cbs[0], cbs[1], None), "rsai_set_allocator")
+
+
+def use_cuda_allocator() -> None:
+    """Restore cudaMallocAsync / cudaFreeAsync for handles created afterwards.
+
+    The earlier callbacks stay referenced: handles created under them still
+    free through them.
+    """
+    _check(load().rsai_set_allocator(ALLOC_FN(), FREE_FN(), None), "rsai_set_allocator")
 
 
 def status_string(status: int) -> str:

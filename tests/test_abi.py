@@ -78,3 +78,15 @@ def test_no_device_status(lib):
         pytest.skip("a GPU is visible")
     v = ctypes.c_double(0.0)
     assert lib.rsai_peak_fma(0, None, ctypes.byref(v)) == 12
+
+
+def test_set_allocator_arguments(lib):
+    """Both callbacks or neither; installing and removing needs no device."""
+    seen = []
+    alloc = rsai.ALLOC_FN(lambda nbytes, stream, ctx: seen.append(nbytes) or None)
+    free = rsai.FREE_FN(lambda ptr, nbytes, stream, ctx: None)
+    assert lib.rsai_set_allocator(alloc, rsai.FREE_FN(), None) == 1
+    assert lib.rsai_set_allocator(rsai.ALLOC_FN(), free, None) == 1
+    assert lib.rsai_set_allocator(alloc, free, None) == 0
+    assert lib.rsai_set_allocator(rsai.ALLOC_FN(), rsai.FREE_FN(), None) == 0
+    assert seen == []  # nothing allocated by installing

@@ -331,3 +331,32 @@ def test_pool_overflow_reruns_only_failed_columns(precision):
         same = np.array([np.array_equal(rows[cp[k]:cp[k + 1]], ref.column(k)[0]) for k in range(P.n)])
         assert same.mean() >= 0.99
         np.testing.assert_allclose(rho[same], ref.rho[same], rtol=1e-3, atol=1e-9)
+
+
+def test_torch_allocator_backs_the_handle(c1):
+    """With PyTorch's caching allocator installed, the handle's device memory is
+    torch's (it shows in memory_allocated and goes back on free) and the result
+    is the same as with cudaMallocAsync."""
+    kw = dict(PARAMS_C1, drop="fixed")
+    dA = rsai.DeviceMatrix.from_host(c1)
+    ref = rsai.build(dA, **kw)
+    want = [t.cpu().numpy() for t in ref.M()]
+    ref.free()
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    rsai.use_torch_allocator()
+    try:
+        h = rsai.build(dA, **kw)
+        torch.cuda.synchronize()
+        held = torch.cuda.memory_allocated() - before
+        assert held > 0
+        got = [t.cpu().numpy() for t in h.M()]
+        it, relres, status = rsai.bicgstab(dA, h, torch.ones(c1.n, dtype=torch.float64, device="cuda"))[1:]
+        assert status == 0 and relres < 1e-8
+        h.free()
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_allocated() == before
+    finally:
+        rsai.use_cuda_allocator()
+    for a, b in zip(got, want):
+        np.testing.assert_array_equal(a, b)
