@@ -108,6 +108,9 @@ template <typename T> struct Work {
 
 enum ColStatus { COL_DONE = 0, COL_OVERFLOW = 1 };
 
+// Entries of a CSR row loaded together in the row-driven loops
+constexpr int kRowGroup = 4;
+
 // Sort buf[0..len) ascending: registers and shuffles on a warp (up to 256
 // elements), bitonic in shared memory otherwise.
 template <class Team>
@@ -672,16 +675,16 @@ template <class Team, typename T> struct Column {
             const int32_t row = w.S[i];
             const int64_t e0 = A.row_ptr[row], e1 = A.row_ptr[row + 1];
             double acc = 0.0;
-            for (int64_t e = e0; e < e1; e += 4) {
-                int32_t cj[4];
-                double av[4];
+            for (int64_t e = e0; e < e1; e += kRowGroup) {
+                int32_t cj[kRowGroup];
+                double av[kRowGroup];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < kRowGroup; ++u) {
                     cj[u] = (e + u < e1) ? A.col_idx[e + u] : -1;
                     av[u] = (e + u < e1) ? A.val[e + u] : 0.0;
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < kRowGroup; ++u) {
                     int pos = (cj[u] >= 0) ? find_J(cj[u]) : -1;
                     if (pos >= 0) { acc = fma(av[u], w.m[pos], acc); ++cnt; }
                 }
@@ -751,51 +754,26 @@ template <class Team, typename T> struct Column {
         for (int i = me; i < q; i += Team::SIZE) w.rhs[i] = (w.I[i] == k) ? T(1) : T(0);
         team.sync();
         T fro2 = 0;
-        if (cap.hcap) {
-            // row by row: row I[i] of A restricted to the columns in J
-            for (int i = me; i < q; i += Team::SIZE) {
-                const int32_t row = w.I[i];
-                const int64_t e0 = A.row_ptr[row], e1 = A.row_ptr[row + 1];
-                for (int64_t e = e0; e < e1; e += 4) {
-                    int32_t cj[4];
-                    double av[4];
+        // column by column: column J[c] of A (CSC, the entries rows_of_J has just
+        // read) placed by the position of its rows in I
+        for (int c = me; c < p; c += Team::SIZE) {
+            const int32_t j = w.J[c];
+            const int64_t e0 = A.col_ptr[j], e1 = A.col_ptr[j + 1];
+            T *Bc = w.B + (int64_t)c * q;
+            for (int64_t e = e0; e < e1; e += 4) {
+                int32_t ri[4];
+                double av[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        cj[u] = (e + u < e1) ? A.col_idx[e + u] : -1;
-                        av[u] = (e + u < e1) ? A.val[e + u] : 0.0;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int c = (cj[u] >= 0) ? find_J(cj[u]) : -1;
-                        if (c >= 0) {
-                            const T a = (T)av[u];
-                            w.B[(int64_t)c * q + i] = a;
-                            fro2 += a * a;
-                        }
-                    }
+                for (int u = 0; u < 4; ++u) {
+                    ri[u] = (e + u < e1) ? A.row_idx[e + u] : -1;
+                    av[u] = (e + u < e1) ? A.cval[e + u] : 0.0;
                 }
-            }
-        } else {
-            // column by column: column J[c] of A placed by the position of its rows in I
-            for (int c = me; c < p; c += Team::SIZE) {
-                const int32_t j = w.J[c];
-                const int64_t e0 = A.col_ptr[j], e1 = A.col_ptr[j + 1];
-                T *Bc = w.B + (int64_t)c * q;
-                for (int64_t e = e0; e < e1; e += 4) {
-                    int32_t ri[4];
-                    double av[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        ri[u] = (e + u < e1) ? A.row_idx[e + u] : -1;
-                        av[u] = (e + u < e1) ? A.cval[e + u] : 0.0;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        if (ri[u] >= 0) {
-                            T a = (T)av[u];
-                            Bc[find_i32(w.I, q, ri[u])] = a;
-                            fro2 += a * a;
-                        }
+                for (int u = 0; u < 4; ++u) {
+                    if (ri[u] >= 0) {
+                        T a = (T)av[u];
+                        Bc[find_i32(w.I, q, ri[u])] = a;
+                        fro2 += a * a;
                     }
                 }
             }

@@ -24,6 +24,71 @@ template <typename T> __device__ __forceinline__ T warp_sum_t(T x) {
     return x;
 }
 
+__host__ __device__ constexpr int ilog2_c(int m) { return m <= 1 ? 0 : 1 + ilog2_c(m >> 1); }
+
+// All-reduce of M values (M a power of two <= 32) over the warp: on entry
+// lane l holds partial sums x[0..M); on exit every lane holds the M totals.
+// Reduce-scatter by recursive halving (at the level with xor distance o the
+// lanes with bit o set keep the upper half of their values, the others the
+// lower half, and each adds its partner's copy of the half it keeps), plain
+// butterfly levels once a lane holds one value, then an all-gather from the
+// lanes that own each total.  M - 1 + (5 - log2 M) + M shuffles and
+// 4 + M - log2 M additions instead of 5 M of each for M separate reductions.
+template <int M, typename T> __device__ __forceinline__ void warp_allreduce_vec(T (&x)[M]) {
+    constexpr int L = ilog2_c(M);
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int lv = 0; lv < L; ++lv) {
+        const int o = 16 >> lv;
+        const int h = M >> (lv + 1);
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int t = 0; t < h; ++t) {
+            const T send = upper ? x[t] : x[t + h];
+            const T keep = upper ? x[t + h] : x[t];
+            x[t] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+#pragma unroll
+    for (int o = 16 >> L; o > 0; o >>= 1) x[0] += __shfl_xor_sync(0xffffffffu, x[0], o);
+    if (M == 1) return;
+    const T mine = x[0];
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+        int src = 0;
+#pragma unroll
+        for (int lv = 0; lv < L; ++lv) src |= ((c >> (L - 1 - lv)) & 1) << (4 - lv);
+        x[c] = __shfl_sync(0xffffffffu, mine, src);
+    }
+}
+
+// One Householder update on the register tile: the dot products of v with
+// the trailing columns j+1..15 and with rhs (16 - j values, all-reduced
+// together in a block of M >= 16 - j), then C <- C - (2 / v^T v) v (v^T C).
+template <int M, typename T>
+__device__ __forceinline__ void step_update(int j, T (&b0)[kSmallP], T (&b1)[kSmallP], T &r0, T &r1, T v0, T v1,
+                                            T two_over) {
+    T x[M];
+#pragma unroll
+    for (int u = 0; u < M; ++u) {
+        const int c = j + 1 + u;
+        x[u] = (c < kSmallP) ? v0 * b0[c] + v1 * b1[c] : ((c == kSmallP) ? v0 * r0 + v1 * r1 : T(0));
+    }
+    warp_allreduce_vec<M>(x);
+#pragma unroll
+    for (int u = 0; u < M; ++u) {
+        const int c = j + 1 + u;
+        const T f = x[u] * two_over;
+        if (c < kSmallP) {
+            b0[c] -= f * v0;
+            b1[c] -= f * v1;
+        } else if (c == kSmallP) {
+            r0 -= f * v0;
+            r1 -= f * v1;
+        }
+    }
+}
+
 // Householder QR of B (q x p, ld q) applied to rhs, then back substitution into
 // rhs[0..p).  vhead/vtv receive v_j(j) and v_j^T v_j.  Returns the rank flag.
 //
@@ -59,24 +124,13 @@ __device__ __noinline__ int warp_qr_small(T *B, int q, int p, T *rhs, T *vhead, 
             if (lane == j) v0 = vh;
             {
                 const T two_over = (vv > T(0)) ? T(2) / vv : T(0);
-                T d[kSmallP + 1];
-#pragma unroll
-                for (int c = j + 1; c < kSmallP; ++c) d[c] = v0 * b0[c] + v1 * b1[c];
-                d[kSmallP] = v0 * r0 + v1 * r1;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-                    for (int c = j + 1; c <= kSmallP; ++c) d[c] += __shfl_xor_sync(0xffffffffu, d[c], o);
-                }
-#pragma unroll
-                for (int c = j + 1; c < kSmallP; ++c) {
-                    const T f = d[c] * two_over;
-                    b0[c] -= f * v0;
-                    b1[c] -= f * v1;
-                }
-                const T fr = d[kSmallP] * two_over;
-                r0 -= fr * v0;
-                r1 -= fr * v1;
+                // j is a constant in each unrolled step, so one branch survives
+                const int m = kSmallP - j;
+                if (m > 8) step_update<16>(j, b0, b1, r0, r1, v0, v1, two_over);
+                else if (m > 4) step_update<8>(j, b0, b1, r0, r1, v0, v1, two_over);
+                else if (m > 2) step_update<4>(j, b0, b1, r0, r1, v0, v1, two_over);
+                else if (m > 1) step_update<2>(j, b0, b1, r0, r1, v0, v1, two_over);
+                else step_update<1>(j, b0, b1, r0, r1, v0, v1, two_over);
             }
             if (lane == j) b0[j] = alpha;  // R_jj; rows > j keep the reflector tail
             if (lane == 0) {
