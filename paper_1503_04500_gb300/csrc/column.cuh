@@ -42,7 +42,7 @@ struct Caps {
 };
 
 template <typename T> struct Work {
-    T *B, *vhead, *vtv, *rhs;
+    T *B, *vhead, *tau, *rhs;
     double *m, *r, *z, *wv;
     long long *ctr;
     int32_t *I, *S, *J, *Jn, *Rset, *buf, *buf2, *Rhat, *hkey, *hval;
@@ -79,7 +79,7 @@ template <typename T> struct Work {
         size_t o = 0;
         B = (T *)(base + o); o += align16(sizeof(T) * (size_t)c.bcap);
         vhead = (T *)(base + o); o += align16(sizeof(T) * (size_t)c.pcap);
-        vtv = (T *)(base + o); o += align16(sizeof(T) * (size_t)c.pcap);
+        tau = (T *)(base + o); o += align16(sizeof(T) * (size_t)c.pcap);
         rhs = (T *)(base + o); o += align16(sizeof(T) * (size_t)(c.qcap + 1));
         m = (double *)(base + o); o += align16(sizeof(double) * (size_t)c.pcap);
         r = (double *)(base + o); o += align16(sizeof(double) * (size_t)(c.qcap + 1));
@@ -158,7 +158,7 @@ __device__ void back_substitute_team(const Team &team, const T *B, int q, int p,
 
 // Householder QR of B (q x p, column-major, ld q) applied to rhs, then back
 // substitution into rhs[0..p).  Keeps the reflectors (v_j below the diagonal
-// of B, heads in vhead, v^T v in vtv) for the refinement solve.  Returns the
+// of B, heads in vhead, tau = 2 / v^T v in tau) for the refinement solve.  Returns the
 // rank flag.  Team-generic: the norm of the pivot column is one team
 // reduction; the trailing columns (and rhs) are dealt out to the team's warps,
 // each warp forming its column's dot product with the reflector (lanes over
@@ -170,7 +170,7 @@ __device__ void back_substitute_team(const Team &team, const T *B, int q, int p,
 // each warp forming its column's dot product (lanes over rows, one warp
 // reduction) and applying the update itself.  Stores R_jj, v_j(j), v_j^T v_j.
 template <class Team, typename T>
-__device__ __forceinline__ void householder_step(const Team &team, T *B, int q, int p, T *rhs, T *vhead, T *vtvs,
+__device__ __forceinline__ void householder_step(const Team &team, T *B, int q, int p, T *rhs, T *vhead, T *taus,
                                                  int j, int c_begin, T small, int &rank_flag) {
     const int me = team.rank();
     const int lane = me & 31, wid = me >> 5;
@@ -184,8 +184,8 @@ __device__ __forceinline__ void householder_step(const Team &team, T *B, int q, 
     const T alpha = (x0 >= T(0)) ? -nrm : nrm;
     const T v0 = x0 - alpha;
     const T vtv = sigma - x0 * x0 + v0 * v0;
-    if (vtv > T(0)) {
-        const T two_over = T(2) / vtv;
+    const T two_over = (vtv > T(0)) ? T(2) / vtv : T(0);
+    if (two_over > T(0)) {
         for (int c = c_begin + wid; c <= p; c += NW) {
             T *t = (c < p) ? B + (int64_t)c * q : rhs;
             T d = 0;
@@ -200,7 +200,7 @@ __device__ __forceinline__ void householder_step(const Team &team, T *B, int q, 
     if (me == 0) {
         col[j] = alpha;
         vhead[j] = v0;
-        vtvs[j] = vtv;
+        taus[j] = two_over;
     }
     rank_flag |= (fabs(alpha) <= small) ? 1 : 0;
     team.sync();
@@ -208,12 +208,12 @@ __device__ __forceinline__ void householder_step(const Team &team, T *B, int q, 
 
 // Householder QR of B (q x p, column-major, ld q) applied to rhs, then back
 // substitution into rhs[0..p).  Keeps the reflectors (v_j below the diagonal
-// of B, heads in vhead, v^T v in vtv) for the refinement solve.  Returns the
+// of B, heads in vhead, tau = 2 / v^T v in tau) for the refinement solve.  Returns the
 // rank flag.  Team-generic, one team synchronisation per step; not inlined.
 template <class Team, typename T>
-__device__ __noinline__ int qr_solve_team(Team team, T *B, int q, int p, T *rhs, T *vhead, T *vtvs, T small) {
+__device__ __noinline__ int qr_solve_team(Team team, T *B, int q, int p, T *rhs, T *vhead, T *taus, T small) {
     int rank_flag = 0;
-    for (int j = 0; j < p; ++j) householder_step(team, B, q, p, rhs, vhead, vtvs, j, j + 1, small, rank_flag);
+    for (int j = 0; j < p; ++j) householder_step(team, B, q, p, rhs, vhead, taus, j, j + 1, small, rank_flag);
     back_substitute_team(team, B, q, p, rhs, small);
     return rank_flag;
 }
@@ -222,10 +222,10 @@ __device__ __noinline__ int qr_solve_team(Team team, T *B, int q, int p, T *rhs,
 // left holding Q^T rhs): a factor from scratch (j_start = 0) that is kept for
 // later updates, or the appended block of the QR update.  Not inlined.
 template <class Team, typename T>
-__device__ __noinline__ int qr_factor_team(Team team, T *B, int q, int p, T *rhs, T *vhead, T *vtvs, T small,
+__device__ __noinline__ int qr_factor_team(Team team, T *B, int q, int p, T *rhs, T *vhead, T *taus, T small,
                                            int j_start) {
     int rank_flag = 0;
-    for (int j = j_start; j < p; ++j) householder_step(team, B, q, p, rhs, vhead, vtvs, j, j + 1, small, rank_flag);
+    for (int j = j_start; j < p; ++j) householder_step(team, B, q, p, rhs, vhead, taus, j, j + 1, small, rank_flag);
     return rank_flag;
 }
 
@@ -233,12 +233,12 @@ constexpr int kPanel = 16;
 
 // Compact-WY pieces shared by the panel factorization and the QR update.
 // V: nb explicit reflectors (zeros above the diagonal, heads on it) of
-// length qq in shared memory, ld qq; vtv: their v^T v.
+// length qq in shared memory, ld qq; taus: their 2 / v^T v.
 // T (kPanel x kPanel in tm) of H_0 ... H_{nb-1} = I - V T V^T:
 // y(s,t) = v_s^T v_t (s < t), then column by column
 // T(t,t) = tau_t, T(0:t, t) = -tau_t T(0:t, 0:t) y(0:t, t).
 template <class Team, typename T>
-__device__ __forceinline__ void wy_form_T(const Team &team, const T *V, int qq, int nb, const T *vtv, T *tm) {
+__device__ __forceinline__ void wy_form_T(const Team &team, const T *V, int qq, int nb, const T *taus, T *tm) {
     const int me = team.rank();
     const int lane = me & 31, wid = me >> 5;
     constexpr int NW = (Team::SIZE + 31) / 32;
@@ -254,8 +254,7 @@ __device__ __forceinline__ void wy_form_T(const Team &team, const T *V, int qq, 
     }
     team.sync();
     for (int t = 0; t < nb; ++t) {
-        const T vv = vtv[t];
-        const T tau = (vv > T(0)) ? T(2) / vv : T(0);
+        const T tau = taus[t];
         T val = T(0);
         if (me < t) {
             T acc = 0;
@@ -358,7 +357,7 @@ __device__ __forceinline__ void wy_apply(const Team &team, const T *V, int qq, i
 // factor whose first j_start columns are done, Section 3); backsub = false
 // leaves Q^T rhs in rhs.
 template <class Team, typename T>
-__device__ __noinline__ int qr_solve_staged(Team team, T *B, int q, int p, T *rhs, T *vhead, T *vtvs, T small,
+__device__ __noinline__ int qr_solve_staged(Team team, T *B, int q, int p, T *rhs, T *vhead, T *taus, T small,
                                             T *stage, int stage_bytes,
                                             int j_start = 0, bool backsub = true) {
     const int me = team.rank();
@@ -374,7 +373,7 @@ __device__ __noinline__ int qr_solve_staged(Team team, T *B, int q, int p, T *rh
         int nb = (int)min((int64_t)kPanel, velems / (int64_t)max(qq, 1));
         nb = min(nb, p - j0);
         if (nb < 4) {
-            householder_step(team, B, q, p, rhs, vhead, vtvs, j0, j0 + 1, small, rank_flag);
+            householder_step(team, B, q, p, rhs, vhead, taus, j0, j0 + 1, small, rank_flag);
             ++j0;
             continue;
         }
@@ -395,8 +394,8 @@ __device__ __noinline__ int qr_solve_staged(Team team, T *B, int q, int p, T *rh
             const T alpha = (x0 >= T(0)) ? -nrm : nrm;
             const T v0 = x0 - alpha;
             const T vtv = sigma - x0 * x0 + v0 * v0;
-            if (vtv > T(0)) {
-                const T two_over = T(2) / vtv;
+            const T two_over = (vtv > T(0)) ? T(2) / vtv : T(0);
+            if (two_over > T(0)) {
                 for (int c = t + 1 + wid; c < nb; c += NW) {
                     T *cc = V + (int64_t)c * qq;
                     T d = 0;
@@ -411,7 +410,7 @@ __device__ __noinline__ int qr_solve_staged(Team team, T *B, int q, int p, T *rh
             if (me == 0) {
                 col[t] = alpha;
                 vhead[j0 + t] = v0;
-                vtvs[j0 + t] = vtv;
+                taus[j0 + t] = two_over;
             }
             rank_flag |= (fabs(alpha) <= small) ? 1 : 0;
             team.sync();
@@ -430,7 +429,7 @@ __device__ __noinline__ int qr_solve_staged(Team team, T *B, int q, int p, T *rh
         for (int e = me; e < kPanel * kPanel; e += Team::SIZE) tm[e] = T(0);
         team.sync();
         // 5. T, 6. trailing columns and rhs, rows j0..q-1
-        wy_form_T(team, V, qq, nb, vtvs + j0, tm);
+        wy_form_T(team, V, qq, nb, taus + j0, tm);
         wy_apply(team, V, qq, nb, tm, B, q, p, rhs, j0, j0 + nb, p);
         j0 += nb;
     }
@@ -441,17 +440,17 @@ __device__ __noinline__ int qr_solve_staged(Team team, T *B, int q, int p, T *rh
 // rhs <- Q^T rhs with the stored reflectors, then R^{-1}; not inlined
 template <class Team, typename T>
 __device__ __noinline__ void apply_qt_team(Team team, const T *B, int q, int p, T *rhs, const T *vhead,
-                                           const T *vtvs, T small) {
+                                           const T *taus, T small) {
     const int me = team.rank();
     for (int j = 0; j < p; ++j) {
         const T *col = B + (int64_t)j * q;
-        T v0 = vhead[j], vtv = vtvs[j];
-        if (vtv > T(0)) {
+        const T v0 = vhead[j], tau = taus[j];
+        if (tau > T(0)) {
             T d = 0;
             for (int i = me; i < q; i += Team::SIZE)
                 if (i >= j) d += ((i == j) ? v0 : col[i]) * rhs[i];
             T sdot = team.sum(d);
-            T f = sdot * (T(2) / vtv);
+            T f = sdot * tau;
             for (int i = me; i < q; i += Team::SIZE)
                 if (i >= j) rhs[i] -= f * ((i == j) ? v0 : col[i]);
         }
@@ -468,7 +467,7 @@ __device__ __noinline__ void apply_qt_team(Team team, const T *B, int q, int p, 
 // not fit four reflectors) one reflector per pass, one warp per column.
 template <class Team, typename T>
 __device__ __noinline__ void qr_update_apply(Team team, T *B, int q, int p, int q0, int p0, const T *vhead,
-                                             const T *vtvs, T *stage, int stage_bytes) {
+                                             const T *taus, T *stage, int stage_bytes) {
     const int me = team.rank();
     const int lane = me & 31, wid = me >> 5;
     constexpr int NW = (Team::SIZE + 31) / 32;
@@ -482,9 +481,8 @@ __device__ __noinline__ void qr_update_apply(Team team, T *B, int q, int p, int 
         nb = min(nb, p0 - j0);
         if (nb < 4) {
             const T *col = B + (int64_t)j0 * q;
-            const T v0 = vhead[j0], vtv = vtvs[j0];
-            if (vtv > T(0)) {
-                const T two_over = T(2) / vtv;
+            const T v0 = vhead[j0], two_over = taus[j0];
+            if (two_over > T(0)) {
                 for (int c = p0 + wid; c < p; c += NW) {
                     T *t = B + (int64_t)c * q;
                     T d = 0;
@@ -505,7 +503,7 @@ __device__ __noinline__ void qr_update_apply(Team team, T *B, int q, int p, int 
         }
         for (int e = me; e < kPanel * kPanel; e += Team::SIZE) tm[e] = T(0);
         team.sync();
-        wy_form_T(team, V, qq, nb, vtvs + j0, tm);
+        wy_form_T(team, V, qq, nb, taus + j0, tm);
         wy_apply(team, V, qq, nb, tm, B, q, p, (T *)nullptr, j0, p0, p - 1);
         j0 += nb;
     }
@@ -524,7 +522,7 @@ template <class Team, typename T> struct Column {
     double rho;
     T small_last;  // rank threshold of the last solve (reused by the adjoint)
     T fro2_f;      // ||B||_F^2 of the kept factor (Caps::append)
-    bool fact_valid;  // B, vhead, vtv, qte, Ip, Jp hold the factor of the current J (Caps::append)
+    bool fact_valid;  // B, vhead, tau, qte, Ip, Jp hold the factor of the current J (Caps::append)
     // per-column work counters (integers; committed only when the column finishes)
     long long c_qr, c_res, c_ref, c_ref64, c_bytes;
     int c_solves, c_drops, c_pmax, c_qmax;
@@ -600,22 +598,22 @@ template <class Team, typename T> struct Column {
     }
 
     // Householder QR of B (q x p, ld q) applied to rhs, then back substitution
-    // into rhs[0..p); the reflectors stay in B (tails), vhead and vtv.
+    // into rhs[0..p); the reflectors stay in B (tails), vhead and tau.
     __device__ void qr_solve(T small) {
         if constexpr (std::is_same<Team, WarpTeam>::value) {
             if (p > 2 && p <= cap.small_p && q <= kSmallQ) {
-                rank_flag = warp_qr_small(w.B, q, p, w.rhs, w.vhead, w.vtv, small);
+                rank_flag = warp_qr_small(w.B, q, p, w.rhs, w.vhead, w.tau, small);
                 return;
             }
         }
         if constexpr (!std::is_same<Team, WarpTeam>::value) {
             const bool keep = cap.append != 0;  // keep Q^T e_k for later updates
             if (cap.stage_bytes > 0 && p >= 2 * kPanel)
-                rank_flag = qr_solve_staged<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.vtv, small, (T *)w.stage,
+                rank_flag = qr_solve_staged<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.tau, small, (T *)w.stage,
                                                      cap.stage_bytes, 0, !keep);
             else
-                rank_flag = keep ? qr_factor_team<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.vtv, small, 0)
-                                 : qr_solve_team<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.vtv, small);
+                rank_flag = keep ? qr_factor_team<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.tau, small, 0)
+                                 : qr_solve_team<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.tau, small);
             if (keep) {
                 // a factor from scratch: factor order = sorted order
                 const int me = team.rank();
@@ -630,7 +628,7 @@ template <class Team, typename T> struct Column {
             }
             return;
         }
-        rank_flag = qr_solve_team<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.vtv, small);
+        rank_flag = qr_solve_team<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.tau, small);
     }
 
     // factor row of sorted I position i / factor column of sorted J position c
@@ -647,11 +645,11 @@ template <class Team, typename T> struct Column {
     __device__ void apply_qt_solve(T small) {
         if constexpr (std::is_same<Team, WarpTeam>::value) {
             if (p > 2 && p <= cap.small_p && q <= kSmallQ) {
-                warp_apply_qt_small(w.B, q, p, w.rhs, w.vhead, w.vtv, small);
+                warp_apply_qt_small(w.B, q, p, w.rhs, w.vhead, w.tau, small);
                 return;
             }
         }
-        apply_qt_team<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.vtv, small);
+        apply_qt_team<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.tau, small);
     }
 
     // S = I u {k}; r = A(:,J) m - e_k on S in double (Eq. 2.4), row by row
@@ -896,12 +894,12 @@ template <class Team, typename T> struct Column {
             if (ik < q && w.I[ik] == k && w.Ip[ik] >= qo) w.qte[w.Ip[ik]] = T(1);
         }
         team.sync();
-        qr_update_apply<Team, T>(team, w.B, q, p, qo, po, w.vhead, w.vtv, (T *)w.stage, cap.stage_bytes);
+        qr_update_apply<Team, T>(team, w.B, q, p, qo, po, w.vhead, w.tau, (T *)w.stage, cap.stage_bytes);
         if (cap.stage_bytes > 0 && p >= 2 * kPanel)
-            qr_solve_staged<Team, T>(team, w.B, q, p, w.qte, w.vhead, w.vtv, small, (T *)w.stage, cap.stage_bytes,
+            qr_solve_staged<Team, T>(team, w.B, q, p, w.qte, w.vhead, w.tau, small, (T *)w.stage, cap.stage_bytes,
                                      po, false);
         else
-            qr_factor_team<Team, T>(team, w.B, q, p, w.qte, w.vhead, w.vtv, small, po);
+            qr_factor_team<Team, T>(team, w.B, q, p, w.qte, w.vhead, w.tau, small, po);
         int rf = 0;
         for (int j = me; j < p; j += Team::SIZE) rf |= (fabs(w.B[(int64_t)j * q + j]) <= small) ? 1 : 0;
         rank_flag = team.sum(rf) > 0 ? 1 : 0;

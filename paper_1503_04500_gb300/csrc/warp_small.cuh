@@ -90,14 +90,16 @@ __device__ __forceinline__ void step_update(int j, T (&b0)[kSmallP], T (&b1)[kSm
 }
 
 // Householder QR of B (q x p, ld q) applied to rhs, then back substitution into
-// rhs[0..p).  vhead/vtv receive v_j(j) and v_j^T v_j.  Returns the rank flag.
+// rhs[0..p).  vhead/tau receive v_j(j) and 2 / v_j^T v_j.  Returns the rank
+// flag.  The back substitution multiplies by reciprocals of the diagonal of R
+// formed once, one per lane, instead of dividing at each of its steps.
 //
 // Columns p..15 are zero-filled, so every operation on them is a no-op: the
 // unrolled loops run branch-free over all 16 slots; only the steps j >= p are
 // skipped.  Not inlined: the unrolled body is large and the column algorithm
 // calls the solve from several places.
 template <typename T>
-__device__ __noinline__ int warp_qr_small(T *B, int q, int p, T *rhs, T *vhead, T *vtv, T small) {
+__device__ __noinline__ int warp_qr_small(T *B, int q, int p, T *rhs, T *vhead, T *tau, T small) {
     const int lane = threadIdx.x & 31;
     const bool h0 = lane < q, h1 = lane + 32 < q;
     T b0[kSmallP], b1[kSmallP];
@@ -108,6 +110,7 @@ __device__ __noinline__ int warp_qr_small(T *B, int q, int p, T *rhs, T *vhead, 
     }
     T r0 = h0 ? rhs[lane] : T(0);
     T r1 = h1 ? rhs[lane + 32] : T(0);
+    T dg = T(0);  // R_ll in lane l
     int rank = 0;
 #pragma unroll
     for (int j = 0; j < kSmallP; ++j) {
@@ -122,8 +125,8 @@ __device__ __noinline__ int warp_qr_small(T *B, int q, int p, T *rhs, T *vhead, 
             const T vh = x0 - alpha;
             const T vv = sigma - x0 * x0 + vh * vh;
             if (lane == j) v0 = vh;
+            const T two_over = (vv > T(0)) ? T(2) / vv : T(0);
             {
-                const T two_over = (vv > T(0)) ? T(2) / vv : T(0);
                 // j is a constant in each unrolled step, so one branch survives
                 const int m = kSmallP - j;
                 if (m > 8) step_update<16>(j, b0, b1, r0, r1, v0, v1, two_over);
@@ -132,22 +135,26 @@ __device__ __noinline__ int warp_qr_small(T *B, int q, int p, T *rhs, T *vhead, 
                 else if (m > 1) step_update<2>(j, b0, b1, r0, r1, v0, v1, two_over);
                 else step_update<1>(j, b0, b1, r0, r1, v0, v1, two_over);
             }
-            if (lane == j) b0[j] = alpha;  // R_jj; rows > j keep the reflector tail
+            if (lane == j) {
+                b0[j] = alpha;  // R_jj; rows > j keep the reflector tail
+                dg = alpha;
+            }
             if (lane == 0) {
                 vhead[j] = vh;
-                vtv[j] = vv;
+                tau[j] = two_over;
             }
             rank |= (fabs(alpha) <= small) ? 1 : 0;
         }
     }
     // back substitution on R (row i of R lives in lane i, slot b0)
+    const T rdi = (fabs(dg) <= small) ? T(0) : T(1) / dg;
     T x = T(0);
 #pragma unroll
     for (int i = kSmallP - 1; i >= 0; --i) {
         if (i < p) {
-            const T di = __shfl_sync(0xffffffffu, b0[i], i);
+            const T ri = __shfl_sync(0xffffffffu, rdi, i);
             const T yi = __shfl_sync(0xffffffffu, r0, i);
-            const T xi = (fabs(di) <= small) ? T(0) : yi / di;
+            const T xi = (ri == T(0)) ? T(0) : yi * ri;
             if (lane == i) x = xi;
             if (lane < i) r0 -= b0[i] * xi;
         }
@@ -164,9 +171,9 @@ __device__ __noinline__ int warp_qr_small(T *B, int q, int p, T *rhs, T *vhead, 
     return rank;
 }
 
-// rhs <- R^{-1} Q^T rhs with the reflectors left in B by warp_qr_small
+// rhs <- R^{-1} Q^T rhs with the reflectors left in B, vhead and tau by warp_qr_small
 template <typename T>
-__device__ __noinline__ void warp_apply_qt_small(const T *B, int q, int p, T *rhs, const T *vhead, const T *vtv,
+__device__ __noinline__ void warp_apply_qt_small(const T *B, int q, int p, T *rhs, const T *vhead, const T *tau,
                                                  T small) {
     const int lane = threadIdx.x & 31;
     const bool h0 = lane < q, h1 = lane + 32 < q;
@@ -177,22 +184,25 @@ __device__ __noinline__ void warp_apply_qt_small(const T *B, int q, int p, T *rh
     for (int j = 0; j < kSmallP; ++j) {
         const bool live = j < p;
         rrow[j] = (live && h0) ? B[j * q + lane] : T(0);
-        const T vv = live ? vtv[j] : T(0);
+        const T tv = live ? tau[j] : T(0);
         const T vh = live ? vhead[j] : T(0);
         T v0 = (lane > j) ? rrow[j] : ((lane == j) ? vh : T(0));
         T v1 = (live && h1) ? B[j * q + lane + 32] : T(0);
         const T d = warp_sum_t(v0 * r0 + v1 * r1);
-        const T f = (vv > T(0)) ? d * (T(2) / vv) : T(0);
+        const T f = (tv > T(0)) ? d * tv : T(0);
         r0 -= f * v0;
         r1 -= f * v1;
     }
+    // reciprocal of R_ll in lane l, as in warp_qr_small
+    const T dl = (lane < p) ? B[lane * q + lane] : T(0);
+    const T rdi = (fabs(dl) <= small) ? T(0) : T(1) / dl;
     T x = T(0);
 #pragma unroll
     for (int i = kSmallP - 1; i >= 0; --i) {
         if (i < p) {
-            const T di = __shfl_sync(0xffffffffu, rrow[i], i);
+            const T ri = __shfl_sync(0xffffffffu, rdi, i);
             const T yi = __shfl_sync(0xffffffffu, r0, i);
-            const T xi = (fabs(di) <= small) ? T(0) : yi / di;
+            const T xi = (ri == T(0)) ? T(0) : yi * ri;
             if (lane == i) x = xi;
             if (lane < i) r0 -= rrow[i] * xi;
         }
