@@ -318,9 +318,7 @@ void rsai_handle_free(rsai_handle *h);
  * rsai_set_allocator -- where the library takes its device memory from.
  *
  * No counterpart in the paper: the plumbing that lets a host framework (for
- * example PyTorch's caching allocator) own every device buffer of the library,
- * as the survey of the interface asks (workspace through an optional
- * allocator callback).
+ * example PyTorch's caching allocator) own every device buffer of the library.
  *
  * alloc(bytes, stream, ctx) returns a device pointer (aligned to at least 256
  * bytes) usable in stream order on `stream`, or NULL when out of memory (the
