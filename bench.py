@@ -242,6 +242,7 @@ def main():
         return [a.elapsed_time(b) for a, b in ms]
 
     from paper_1503_04500_gb300 import autotune
+    from paper_1503_04500_gb300.autograd import Pattern, preconditioned_solve_loss
 
     h32 = rsai.build(dA, precision="fp32_refine", **PARAMS)
     h64 = rsai.build(dA, precision="fp64", **PARAMS)
@@ -396,6 +397,26 @@ def main():
             b_ms = statistics.median(bt)
             c4[prec] = {"fwd_ms": f_ms, "bwd_ms": b_ms, "bwd_fwd_ratio": b_ms / f_ms,
                         "columns_per_s": P4.base.n / (f_ms / 1e3), "frob": h4.stats()["frob"]}
+            # loss_2 = ||b - A M y_20||^2 (20 BiCGStab iterations) and its gradient in the values of A
+            patA, patM = Pattern.of_matrix(P4.base), Pattern.of_M(h4)
+            b4 = torch.as_tensor(inputs.ones_rhs(P4.base), device="cuda")
+            lt = {"fwd": [], "fwd_bwd": []}
+            for rep in range(4):
+                for kind in ("fwd", "fwd_bwd"):
+                    av = d4.val.clone().requires_grad_(kind == "fwd_bwd")
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(st4)
+                    L2 = preconditioned_solve_loss(av, h4, patA, patM, b4, 20)
+                    if kind == "fwd_bwd":
+                        L2.backward()
+                    e1.record(st4)
+                    torch.cuda.synchronize()
+                    if rep > 0:
+                        lt[kind].append(e0.elapsed_time(e1))
+            c4[prec]["loss2_y20"] = {"value": L2.item(), "fwd_ms": statistics.median(lt["fwd"]),
+                                     "fwd_bwd_ms": statistics.median(lt["fwd_bwd"])}
             h4.free()
 
     cpu = None

@@ -315,6 +315,38 @@ rsai_status rsai_set_tuning(rsai_handle *h, const rsai_tuning *t);
 void rsai_handle_free(rsai_handle *h);
 
 /*
+ * rsai_get_M_csc -- M's pattern in CSC, as the build assembled it:
+ * col_ptr[n+1] (int64), row_idx[nnz_M] (int32, ascending within a column)
+ * and csc_to_csr[nnz_M] (int64): the position in rsai_get_M's CSR value array
+ * of each CSC entry, so that the CSC values of M (or of any array in M's CSR
+ * order, such as rsai_refit's output) are val_csr[csc_to_csr[e]].  Any
+ * pointer may be NULL.  Host or device destinations; synchronises the stream.
+ * With it, products with M^T are CSR products over (col_ptr, row_idx).
+ */
+rsai_status rsai_get_M_csc(rsai_handle *h, int64_t *col_ptr, int32_t *row_idx, int64_t *csc_to_csr, void *stream);
+
+/*
+ * rsai_spmv -- y = A x for a CSR matrix on the device (Eq. 1.2 applies A and
+ * M by such products; BiCGStab, Section 5).  A->row_ptr/col_idx/val, x and y
+ * are device pointers; y is overwritten, x and y must not overlap.  A product
+ * with A^T is the same call on A's CSC arrays (col_ptr, row_idx, CSC values)
+ * read as the CSR of A^T.  8 lanes per row, a fixed reduction order (repeated
+ * calls give identical y).  Errors: INVALID_ARG, SHAPE, NO_DEVICE, CUDA.
+ */
+rsai_status rsai_spmv(const rsai_csr *A, const double *x, double *y, void *stream);
+
+/*
+ * rsai_spmv_grad_values -- gval[e] = gy[i] * x[col_idx[e]] for every stored
+ * entry e of row i: the gradient of <gy, A x> with respect to the stored values
+ * of A, in A's CSR order (the adjoint of rsai_spmv in its values; the adjoint
+ * in x is rsai_spmv on A^T).  No counterpart in the paper, which does not
+ * differentiate; it lets a caller differentiate a Krylov solve preconditioned
+ * by M.  A->val is not read.  Device pointers; gval is overwritten.  Errors:
+ * INVALID_ARG, SHAPE, NO_DEVICE, CUDA.
+ */
+rsai_status rsai_spmv_grad_values(const rsai_csr *A, const double *gy, const double *x, double *gval, void *stream);
+
+/*
  * rsai_set_allocator -- where the library takes its device memory from.
  *
  * No counterpart in the paper: the plumbing that lets a host framework (for

@@ -24,6 +24,21 @@ __global__ void k_spmv(int64_t n, const int64_t *__restrict__ row_ptr, const int
     if (row < n && sub == 0) y[row] = acc;
 }
 
+// gval[e] = gy[i] x[col(e)] for every stored entry e of row i: the gradient
+// of y = A x with respect to the stored values of A.  8 lanes per row, one
+// write per entry, no reduction.
+__global__ void k_spmv_grad_values(int64_t n, const int64_t *__restrict__ row_ptr,
+                                   const int32_t *__restrict__ col_idx, const double *__restrict__ gy,
+                                   const double *__restrict__ x, double *__restrict__ gval) {
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t row = g >> 3;
+    int sub = threadIdx.x & 7;
+    if (row >= n) return;
+    const double gr = gy[row];
+    const int64_t a = row_ptr[row], b = row_ptr[row + 1];
+    for (int64_t e = a + sub; e < b; e += 8) gval[e] = gr * x[col_idx[e]];
+}
+
 constexpr int kDotBlocks = 304;
 constexpr int kDotThreads = 256;
 
@@ -53,6 +68,14 @@ __global__ void k_dot_final(const double *partials, double *out) {
         __syncthreads();
     }
     if (threadIdx.x == 0) *out = sh[0];
+}
+
+cudaError_t launch_spmv_grad_values(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const double *gy,
+                                    const double *x, double *gval, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int T = 256;
+    k_spmv_grad_values<<<(unsigned)((n * 8 + T - 1) / T), T, 0, st>>>(n, row_ptr, col_idx, gy, x, gval);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_spmv(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const double *val,

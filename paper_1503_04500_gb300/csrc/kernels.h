@@ -59,6 +59,9 @@ int occupancy_bin_block(bool fp32, const Caps &cap, bool global_work);
 // apply / solver kernels (apply_kernels.cu)
 cudaError_t launch_spmv(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const double *val,
                         const double *x, double *y, cudaStream_t st);
+// gval[e] = gy[row(e)] * x[col(e)] over the stored entries of a CSR matrix
+cudaError_t launch_spmv_grad_values(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const double *gy,
+                                    const double *x, double *gval, cudaStream_t st);
 cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *partials, double *out, cudaStream_t st);
 int bicgstab_run(int64_t n, const int64_t *Arp, const int32_t *Aci, const double *Av, const int64_t *Mrp,
                  const int32_t *Mci, const double *Mv, const double *b, double *x, double rtol, int maxit,

@@ -755,6 +755,39 @@ rsai_status rsai_get_M(rsai_handle *h, int64_t *row_ptr, int32_t *col_idx, doubl
     return (rsai_status)cuda_status(cudaStreamSynchronize(st));
 }
 
+rsai_status rsai_get_M_csc(rsai_handle *h, int64_t *col_ptr, int32_t *row_idx, int64_t *csc_to_csr, void *stream) {
+    if (!h) return RSAI_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t nnzM = 0;
+    if (cudaMemcpyAsync(&nnzM, h->Mcolptr + h->n, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return RSAI_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return RSAI_ERR_CUDA;
+    if (col_ptr && cudaMemcpyAsync(col_ptr, h->Mcolptr, sizeof(int64_t) * (h->n + 1), cudaMemcpyDefault, st))
+        return RSAI_ERR_CUDA;
+    if (row_idx && cudaMemcpyAsync(row_idx, h->Mrows, sizeof(int32_t) * nnzM, cudaMemcpyDefault, st))
+        return RSAI_ERR_CUDA;
+    if (csc_to_csr && cudaMemcpyAsync(csc_to_csr, h->Mcsc_to_csr, sizeof(int64_t) * nnzM, cudaMemcpyDefault, st))
+        return RSAI_ERR_CUDA;
+    return (rsai_status)cuda_status(cudaStreamSynchronize(st));
+}
+
+rsai_status rsai_spmv(const rsai_csr *A, const double *x, double *y, void *stream) {
+    int rc = check_csr_host(A);
+    if (rc != RSAI_OK) return (rsai_status)rc;
+    if (!x || !y) return RSAI_ERR_INVALID_ARG;
+    if (!have_device()) return RSAI_ERR_NO_DEVICE;
+    return (rsai_status)cuda_status(launch_spmv(A->n, A->row_ptr, A->col_idx, A->val, x, y, (cudaStream_t)stream));
+}
+
+rsai_status rsai_spmv_grad_values(const rsai_csr *A, const double *gy, const double *x, double *gval, void *stream) {
+    if (!A || !A->row_ptr || !A->col_idx) return RSAI_ERR_INVALID_ARG;
+    if (A->n <= 0 || A->nnz < 0 || A->n > INT32_MAX) return RSAI_ERR_SHAPE;
+    if (!gy || !x || !gval) return RSAI_ERR_INVALID_ARG;
+    if (!have_device()) return RSAI_ERR_NO_DEVICE;
+    return (rsai_status)cuda_status(
+        launch_spmv_grad_values(A->n, A->row_ptr, A->col_idx, gy, x, gval, (cudaStream_t)stream));
+}
+
 rsai_status rsai_get_columns(rsai_handle *h, double *rho, int32_t *loops, int32_t *flags, void *stream) {
     if (!h) return RSAI_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;

@@ -33,7 +33,7 @@ EXPORTS = [
     "rsai_rebuild", "rsai_set_values", "rsai_get_stats", "rsai_get_M", "rsai_get_columns", "rsai_refit",
     "rsai_apply", "rsai_backward", "rsai_bicgstab", "rsai_handle_free", "rsai_peak_fma", "rsai_build_phase_times",
     "rsai_bicgstab_noalloc", "rsai_build_batch", "rsai_get_block_stats", "rsai_get_tuning", "rsai_set_tuning",
-    "rsai_set_allocator",
+    "rsai_set_allocator", "rsai_get_M_csc", "rsai_spmv", "rsai_spmv_grad_values",
 ]
 
 
@@ -135,6 +135,9 @@ def load(build_if_missing: bool = False):
         "rsai_bicgstab_noalloc": (i32, [ctypes.POINTER(CSR), ctypes.POINTER(CSR), vp, vp, f64, i32,
                                         ctypes.POINTER(i32), ctypes.POINTER(f64), vp]),
         "rsai_set_allocator": (i32, [ALLOC_FN, FREE_FN, vp]),
+        "rsai_get_M_csc": (i32, [vp, vp, vp, vp, vp]),
+        "rsai_spmv": (i32, [ctypes.POINTER(CSR), vp, vp, vp]),
+        "rsai_spmv_grad_values": (i32, [ctypes.POINTER(CSR), vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -286,6 +289,18 @@ class Handle:
         va = torch.empty(max(nnz, 1), dtype=torch.float64, device="cuda")
         _check(load().rsai_get_M(self._h, _ptr(rp), _ptr(ci), _ptr(va), _stream(stream)), "rsai_get_M")
         return rp, ci[:nnz], va[:nnz]
+
+    def M_csc(self, stream=None):
+        """M's pattern in CSC as torch cuda tensors: (col_ptr int64, row_idx int32,
+        csc_to_csr int64), the last giving each CSC entry's position in M's CSR values."""
+        import torch
+
+        nnz = self.stats(stream)["nnz_M"]
+        cp = torch.empty(self.n + 1, dtype=torch.int64, device="cuda")
+        ri = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
+        pos = torch.empty(max(nnz, 1), dtype=torch.int64, device="cuda")
+        _check(load().rsai_get_M_csc(self._h, _ptr(cp), _ptr(ri), _ptr(pos), _stream(stream)), "rsai_get_M_csc")
+        return cp, ri[:nnz], pos[:nnz]
 
     def M_host(self, nnz=None, out=None, stream=None):
         """M in CSR copied straight into host numpy arrays (one D2H copy each)."""
@@ -451,6 +466,29 @@ def bicgstab_noalloc(A: DeviceMatrix, M_csr, b, x, rtol=1e-8, maxit=1000, stream
                                       _stream(stream))
     _check(st, "rsai_bicgstab_noalloc", ok=(RSAI_OK, 10, 11))
     return it.value, rr.value, st
+
+
+def spmv(row_ptr, col_idx, val, x, y=None, stream=None):
+    """rsai_spmv: y = A x for A in CSR (device tensors); returns y."""
+    import torch
+
+    if y is None:
+        y = torch.empty(row_ptr.numel() - 1, dtype=torch.float64, device=x.device)
+    csr = CSR(row_ptr.numel() - 1, col_idx.numel(), _ptr(row_ptr), _ptr(col_idx), _ptr(val))
+    _check(load().rsai_spmv(ctypes.byref(csr), _ptr(x), _ptr(y), _stream(stream)), "rsai_spmv")
+    return y
+
+
+def spmv_grad_values(row_ptr, col_idx, gy, x, gval=None, stream=None):
+    """rsai_spmv_grad_values: gval[e] = gy[row(e)] * x[col(e)] in CSR order; returns gval."""
+    import torch
+
+    if gval is None:
+        gval = torch.empty(col_idx.numel(), dtype=torch.float64, device=x.device)
+    csr = CSR(row_ptr.numel() - 1, col_idx.numel(), _ptr(row_ptr), _ptr(col_idx), None)
+    _check(load().rsai_spmv_grad_values(ctypes.byref(csr), _ptr(gy), _ptr(x), _ptr(gval), _stream(stream)),
+           "rsai_spmv_grad_values")
+    return gval
 
 
 def peak_fma(fp64: bool, stream=None) -> float:
