@@ -123,7 +123,7 @@ typedef struct {
     int64_t solves;       /* LS solves */
     int64_t drops;        /* solves that dropped entries (each costs a re-solve) */
     int32_t p_max, q_max; /* largest LS problem met */
-    int64_t cols_bin[3];  /* columns finished by the warp, CTA and global bins */
+    int64_t cols_bin[3];  /* columns finished by the warp bins (W, W2), the CTA bin and the global bin */
     int64_t n_rank;       /* columns flagged rank deficient */
     int64_t n_nonfinite;  /* columns with a non-finite value */
     int64_t n_failed;     /* columns no bin could hold (then status WORKSPACE) */

@@ -49,8 +49,10 @@ struct rsai_handle {
     double *bfrob2 = nullptr;         // per-block statistics
     long long *bnc = nullptr, *bnnz = nullptr;
     int32_t *err = nullptr;
-    uint32_t *qnext = nullptr;   // [3] queue counters, [3..4] overflow counts
-    int32_t *ovf1 = nullptr, *ovf2 = nullptr;
+    // [0..3] queue counters of bins W, W2, C, G; [4..6] overflow counts W->W2,
+    // W2->C, C->G; [7] columns of a pool-overflow rerun
+    uint32_t *qnext = nullptr;
+    int32_t *ovf1 = nullptr, *ovf2 = nullptr, *ovf3 = nullptr;
     int64_t ovf_cap = 0;
     // per column
     int64_t *col_off = nullptr;
@@ -72,8 +74,8 @@ struct rsai_handle {
     size_t gstride = 0;
     int grid_g = 0;
     // bins
-    Caps capW{}, capC{}, capG{};
-    int grid_w = 0, grid_c = 0;
+    Caps capW{}, capW2{}, capC{}, capG{};
+    int grid_w = 0, grid_w2 = 0, warps_w2 = 0, grid_c = 0;
     rsai_tuning tuning{4, 0, kSmallP, 0};
     // refit / backward scratch (allocated on first use)
     double *fval = nullptr, *fcval = nullptr;
@@ -93,8 +95,9 @@ struct rsai_handle {
 
 namespace {
 
-// layout of the scalar block (8-byte words)
-constexpr int kNorm1 = 0, kTau = 1, kFrob2 = 2, kCtr = 3;
+// layout of the scalar block (8-byte words); words 0 and 1 are unused since
+// ||A||_1 and the drop threshold moved to per-block arrays
+constexpr int kFrob2 = 2, kCtr = 3;
 constexpr int kCounts = kCtr + CTR_COUNT + 3;
 constexpr int kPartial = kCounts + 2;
 constexpr int kScalars = kPartial + kStatBlocks;
@@ -184,17 +187,20 @@ cudaError_t enqueue_bins(rsai_handle *h, int mode, const DevA &A, const Frozen &
                          cudaStream_t st, cudaEvent_t *ev = nullptr, BinHook before_global = nullptr,
                          const int32_t *wlist = nullptr, const uint32_t *wcount = nullptr) {
     const int64_t n = h->n;
-    cudaMemsetAsync(h->qnext, 0, sizeof(uint32_t) * 5, st);  // queue and overflow counters; [5] = retry count
+    cudaMemsetAsync(h->qnext, 0, sizeof(uint32_t) * 7, st);  // queue and overflow counters; [7] = retry count
     const DevParams P = dev_params(h);
     const bool fp32 = h->params.precision == RSAI_FP32_REFINE;
     ColOut O{h->col_off, h->col_len, h->col_q, h->rho, h->loops, h->flags, h->pool_rows, h->pool_vals,
              h->pool_cap, h->pool_top, h->err};
-    ColQueue QW{wlist, wcount, n, h->qnext + 0, h->ovf1, h->qnext + 3, h->ovf_cap};
-    ColQueue QC{h->ovf1, h->qnext + 3, n, h->qnext + 1, h->ovf2, h->qnext + 4, h->ovf_cap};
-    ColQueue QG{h->ovf2, h->qnext + 4, n, h->qnext + 2, nullptr, nullptr, 0};
+    ColQueue QW{wlist, wcount, n, h->qnext + 0, h->ovf1, h->qnext + 4, h->ovf_cap};
+    ColQueue QW2{h->ovf1, h->qnext + 4, n, h->qnext + 1, h->ovf2, h->qnext + 5, h->ovf_cap};
+    ColQueue QC{h->ovf2, h->qnext + 5, n, h->qnext + 2, h->ovf3, h->qnext + 6, h->ovf_cap};
+    ColQueue QG{h->ovf3, h->qnext + 6, n, h->qnext + 3, nullptr, nullptr, 0};
     if (ev) cudaEventRecord(ev[1], st);
     cudaError_t e = launch_bin_warp(mode, fp32, h->grid_w, h->tuning.warp_bin_warps, A, P, h->capW, QW, O, F, gctr,
                                     false, st);
+    if (e != cudaSuccess) return e;
+    e = launch_bin_warp(mode, fp32, h->grid_w2, h->warps_w2, A, P, h->capW2, QW2, O, F, gctr, false, st);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], st);
     e = launch_bin_block(mode, fp32, h->grid_c, A, P, h->capC, QC, O, F, gctr, false, nullptr, 0, 1, st);
@@ -270,7 +276,18 @@ int check_csr_host(const rsai_csr *A) {
     return RSAI_OK;
 }
 
-// choose the capacities of the three bins from the device limits
+// launch shape of bin W2: the warps per CTA of the warp bin, halved until its
+// larger workspace fits
+int plan_w2(rsai_handle *h, bool fp32) {
+    int w = h->tuning.warp_bin_warps, occ = 0;
+    while ((occ = occupancy_bin_warp(fp32, w, h->capW2)) < 1 && w > 1) w /= 2;
+    if (occ < 1) return RSAI_ERR_CUDA;
+    h->warps_w2 = w;
+    h->grid_w2 = h->sms * occ;
+    return RSAI_OK;
+}
+
+// choose the capacities of the four bins from the device limits
 int plan_bins(rsai_handle *h) {
     const bool fp32 = h->params.precision == RSAI_FP32_REFINE;
     int dev = h->device, max_optin = 0;
@@ -281,6 +298,9 @@ int plan_bins(rsai_handle *h) {
     if (occ < 1) return RSAI_ERR_CUDA;
     if (h->tuning.warp_bin_ctas_per_sm > 0) occ = std::min(occ, h->tuning.warp_bin_ctas_per_sm);
     h->grid_w = h->sms * occ;
+    // bin W2: the warp bin's algorithm for |I| <= 128 (B 128 x 32), fewer warps per SM
+    h->capW2 = Caps{128, 32, 512, 64, 128 * 32, 64, h->tuning.small_qr_max_p, 0};
+    if (plan_w2(h, fp32) != RSAI_OK) return RSAI_ERR_CUDA;
     // bin C: shared-memory workspace as large as the opt-in limit allows
     Caps c{1024, 256, 4096, std::min(rneed * 2, 2048), 0, 0, 0, 0, 1};
     size_t base = fp32 ? work_bytes<float>(c) : work_bytes<double>(c);
@@ -363,7 +383,7 @@ namespace {
 // slab (a few tens of MB per CTA) is sized by the first build only.
 int size_global_slab(rsai_handle *h, cudaStream_t st) {
     uint32_t cnt = 0;
-    if (cudaMemcpyAsync(&cnt, h->qnext + 4, sizeof(cnt), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    if (cudaMemcpyAsync(&cnt, h->qnext + 6, sizeof(cnt), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return RSAI_ERR_CUDA;
     int want = std::max(1, std::min(h->sms, (int)cnt));
@@ -415,6 +435,7 @@ int build_common(rsai_handle *h, cudaStream_t st) {
     TRY(dalloc(h, &h->qnext, 8, st));
     TRY(dalloc(h, &h->ovf1, n, st));
     TRY(dalloc(h, &h->ovf2, n, st));
+    TRY(dalloc(h, &h->ovf3, n, st));
     TRY(dalloc(h, &h->col_off, n, st));
     TRY(dalloc(h, &h->col_len, n, st));
     TRY(dalloc(h, &h->col_q, n, st));
@@ -482,14 +503,14 @@ int build_common(rsai_handle *h, cudaStream_t st) {
             TRY(alloc_m(cap));
             // the columns that found the pool full run again (from its current top)
             if (!retry) TRY(dalloc(h, &retry, n, st));
-            cudaMemsetAsync(h->qnext + 5, 0, sizeof(uint32_t), st);
-            k_collect_failed<<<blocks(n, 256), 256, 0, st>>>(h->flags, n, retry, h->qnext + 5);
+            cudaMemsetAsync(h->qnext + 7, 0, sizeof(uint32_t), st);
+            k_collect_failed<<<blocks(n, 256), 256, 0, st>>>(h->flags, n, retry, h->qnext + 7);
             cudaMemsetAsync(h->dscal + kCtr + CTR_FAILED, 0, sizeof(unsigned long long), st);
             cudaMemsetAsync(h->err, 0, sizeof(int32_t), st);
             cudaMemsetAsync(h->row_count, 0, sizeof(int32_t) * (size_t)n, st);
             cudaMemsetAsync(h->cursor, 0, sizeof(int32_t) * (size_t)n, st);
             TRY(cuda_status(enqueue_bins(h, MODE_BUILD, dev_a(h), Frozen{}, h->dscal + kCtr, st, nullptr,
-                                         size_global_slab, retry, h->qnext + 5)));
+                                         size_global_slab, retry, h->qnext + 7)));
             TRY(cuda_status(enqueue_build_tail(h, st, nullptr)));
         }
     }
@@ -981,6 +1002,8 @@ rsai_status rsai_set_tuning(rsai_handle *h, const rsai_tuning *t) {
     }
     if (t->warp_bin_ctas_per_sm > 0) occ = std::min(occ, t->warp_bin_ctas_per_sm);
     h->grid_w = h->sms * occ;
+    h->capW2.small_p = t->small_qr_max_p;
+    if (plan_w2(h, fp32) != RSAI_OK) return RSAI_ERR_CUDA;
     if (t->global_bin_ctas > 0) {
         const int want = std::min(t->global_bin_ctas, h->sms);
         if (want > h->grid_g) {

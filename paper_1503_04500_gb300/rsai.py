@@ -404,6 +404,51 @@ def build(A, c=3, l_max=10, eps=0.3, drop="fixed", tol=1e-3, precision="fp64", t
     return Handle(out.value, int(csr.n), params, st)
 
 
+def transpose(A):
+    """A^T with no arithmetic: A's CSC arrays are the CSR of A^T and its CSR
+    arrays the CSC.  Works on a DeviceMatrix (tensors shared, not copied) and
+    on a SparseMatrix-like host object (its csc_to_csr map is inverted)."""
+    if isinstance(A, DeviceMatrix):
+        return DeviceMatrix(A.n, A.nnz, A.col_ptr, A.row_idx, A.cval, A.row_ptr, A.col_idx, A.val)
+    inv = np.empty_like(A.csc_to_csr)
+    inv[A.csc_to_csr] = np.arange(A.csc_to_csr.size, dtype=A.csc_to_csr.dtype)
+    return dataclasses.replace(A, row_ptr=A.col_ptr, col_idx=A.row_idx, val=A.cval, col_ptr=A.row_ptr,
+                               row_idx=A.col_idx, cval=A.val, csc_to_csr=inv)
+
+
+class LeftHandle:
+    """A left sparse approximate inverse, M A ~ I, kept as the right inverse
+    M_R of A^T built by the same kernels (||M A - I||_F = ||A^T M_R - I||_F,
+    and the column problems of A^T are the row problems of M).  ``right`` is
+    the handle of M_R; M = M_R^T is read through M_R's CSC pattern."""
+
+    def __init__(self, right: Handle):
+        self.right = right
+        self.n = right.n
+
+    def M(self, stream=None):
+        """M = M_R^T in CSR (torch cuda tensors): M_R's CSC arrays, values gathered through csc_to_csr."""
+        _, _, va = self.right.M(stream)
+        cp, ri, pos = self.right.M_csc(stream)
+        return cp, ri, va[pos].contiguous()
+
+    def stats(self, stream=None):
+        """Statistics of M_R (frob = ||A^T M_R - I||_F = ||M A - I||_F)."""
+        return self.right.stats(stream)
+
+    def columns(self, stream=None):
+        """Per row k of M: ||e_k^T - m_k^T A||, loops and flags (those of column k of M_R)."""
+        return self.right.columns(stream)
+
+    def free(self):
+        self.right.free()
+
+
+def build_left(A, **kw) -> LeftHandle:
+    """rsai_build on A^T: a left preconditioner M with M A ~ I (same parameters as ``build``)."""
+    return LeftHandle(build(transpose(A), **kw))
+
+
 def build_batch(members, c=3, l_max=10, eps=0.3, drop="fixed", tol=1e-3, precision="fp64", tie_band=1e-12,
                 stream=None, allow_failed=False) -> Handle:
     """rsai_build_batch over a list of DeviceMatrix (device tensors) or

@@ -1,0 +1,108 @@
+"""Parameter sweeps of RSAI(tol) on the synthetic workloads (the analogue of
+the paper's tables of ε, c and l_max against sparsity, iterations and time,
+Section 5), for the right preconditioner (A M ≈ I) or the left one (M A ≈ I,
+built on Aᵀ by the same kernels).
+
+    python -m paper_1503_04500_gb300.sweep --workload convdiff3d --size 32 \
+        --eps 0.2,0.3,0.4 --c 3,5 --lmax 5,10 --precision fp32_refine
+
+One JSON line per setting: spar = nnz(M)/nnz(A), ||AM - I||_F (or ||MA - I||_F),
+n_c (columns with ||r_k|| > ε), the build time (median of graph-replayed
+rebuilds, CUDA events), and right-preconditioned BiCGStab on A M y = b,
+b = A·1, rtol 1e-8 (iterations and time; right variant only).
+"""
+from __future__ import annotations
+
+import argparse
+import itertools
+import json
+import statistics
+import time
+
+from . import inputs, rsai
+
+
+def _workload(name: str, size: int, seed: int):
+    if name == "convdiff2d":
+        return inputs.convdiff2d(size, (20.0, 20.0))
+    if name == "convdiff3d":
+        return inputs.convdiff3d(size)
+    if name == "powerlaw":
+        return inputs.powerlaw(size, seed=seed)
+    if name == "parametric2d":
+        return inputs.parametric2d(size).base
+    raise ValueError(f"unknown workload {name}")
+
+
+def _floats(s: str):
+    return [float(x) for x in s.split(",") if x]
+
+
+def _ints(s: str):
+    return [int(x) for x in s.split(",") if x]
+
+
+def run(workload="convdiff2d", size=20, seed=1503, eps=(0.3,), c=(3,), lmax=(10,), drop="fixed", tol=1e-3,
+        precision="fp64", side="right", rebuilds=5, solve=True):
+    """Yield one result dict per (eps, c, l_max) setting."""
+    import torch
+
+    A = _workload(workload, size, seed)
+    dA = rsai.DeviceMatrix.from_host(A)
+    b = torch.as_tensor(inputs.ones_rhs(A), device="cuda")
+    st = torch.cuda.current_stream()
+    for e, cc, lm in itertools.product(eps, c, lmax):
+        kw = dict(c=cc, l_max=lm, eps=e, drop=drop, tol=tol, precision=precision)
+        t0 = time.perf_counter()
+        h = rsai.build_left(dA, **kw) if side == "left" else rsai.build(dA, **kw)
+        torch.cuda.synchronize()
+        first_s = time.perf_counter() - t0
+        right = h.right if side == "left" else h
+        times = []
+        for _ in range(rebuilds):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            right.rebuild()
+            e1.record(st)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        s = h.stats()
+        out = {"workload": workload, "n": A.n, "nnz_A": A.nnz, "side": side, "precision": precision, "eps": e,
+               "c": cc, "l_max": lm, "drop": drop, "tol": tol, "spar": s["nnz_M"] / A.nnz, "frob": s["frob"],
+               "n_c": s["n_c"], "p_max": s["p_max"], "q_max": s["q_max"], "cols_bin": s["cols_bin"],
+               "build_ms": statistics.median(times) if times else None, "first_build_s": first_s,
+               "phases_ms": right.phase_times()}
+        if solve and side == "right":
+            t1 = time.perf_counter()
+            _, iters, relres, status = rsai.bicgstab(dA, h, b)
+            torch.cuda.synchronize()
+            out.update({"bicgstab_iters": iters, "bicgstab_relres": relres, "bicgstab_status": status,
+                        "bicgstab_s": time.perf_counter() - t1})
+        h.free()
+        yield out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--workload", default="convdiff2d",
+                    choices=["convdiff2d", "convdiff3d", "powerlaw", "parametric2d"])
+    ap.add_argument("--size", type=int, default=20, help="grid side N (stencils) or n (power law)")
+    ap.add_argument("--seed", type=int, default=1503)
+    ap.add_argument("--eps", default="0.3")
+    ap.add_argument("--c", default="3")
+    ap.add_argument("--lmax", default="10")
+    ap.add_argument("--drop", default="fixed", choices=["none", "adaptive", "fixed"])
+    ap.add_argument("--tol", type=float, default=1e-3)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_refine"])
+    ap.add_argument("--side", default="right", choices=["right", "left"])
+    ap.add_argument("--rebuilds", type=int, default=5)
+    ap.add_argument("--no-solve", dest="solve", action="store_false")
+    a = ap.parse_args(argv)
+    for row in run(a.workload, a.size, a.seed, _floats(a.eps), _ints(a.c), _ints(a.lmax), a.drop, a.tol,
+                   a.precision, a.side, a.rebuilds, a.solve):
+        print(json.dumps(row), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -360,3 +360,38 @@ def test_torch_allocator_backs_the_handle(c1):
         rsai.use_cuda_allocator()
     for a, b in zip(got, want):
         np.testing.assert_array_equal(a, b)
+
+
+def test_left_variant_is_the_transposed_build_of_A_transpose():
+    """build_left: M A ~ I from the same kernels on A^T.  Row k of M is the
+    oracle's column k of the right inverse of A^T (bit-identical pattern, FP64
+    values to 1e-10), and ||M A - I||_F is the build's Frobenius residual."""
+    A = gen.convdiff2d(20, (20.0, 5.0))
+    kw = dict(PARAMS_C1, drop="fixed")
+    left = rsai.build_left(rsai.DeviceMatrix.from_host(A), precision="fp64", **kw)
+    ref = oracle.build(rsai.transpose(A), **kw)
+    rp, ci, va = (t.cpu().numpy() for t in left.M())
+    np.testing.assert_array_equal(rp, ref.colptr)
+    np.testing.assert_array_equal(ci, ref.rows)
+    np.testing.assert_allclose(va, ref.vals, rtol=1e-10, atol=1e-15 * np.abs(ref.vals).max())
+    Md = np.zeros((A.n, A.n))
+    Md[np.repeat(np.arange(A.n), np.diff(rp)), ci] = va
+    frob = np.linalg.norm(Md @ A.to_dense() - np.eye(A.n))
+    np.testing.assert_allclose(left.stats()["frob"], frob, rtol=1e-10)
+    left.free()
+
+
+def test_sweep_rows_and_monotone_residual():
+    """The sweep tool: one row per setting; without dropping, a larger l_max
+    never raises ||AM - I||_F (rho_k is non-increasing over loops), and the
+    left variant's residual equals the right build of A^T."""
+    from paper_1503_04500_gb300 import sweep
+
+    rows = list(sweep.run("convdiff2d", 12, eps=(0.2,), c=(2,), lmax=(2, 6), drop="none", rebuilds=2))
+    assert len(rows) == 2 and all(r["bicgstab_status"] == 0 for r in rows)
+    assert rows[1]["frob"] <= rows[0]["frob"] * (1 + 1e-12)
+    assert rows[1]["spar"] >= rows[0]["spar"]
+    left = list(sweep.run("convdiff2d", 12, eps=(0.2,), c=(2,), lmax=(6,), drop="none", side="left", rebuilds=1))
+    A = gen.convdiff2d(12, (20.0, 20.0))
+    ref = oracle.build(rsai.transpose(A), c=2, l_max=6, eps=0.2, drop="none")
+    np.testing.assert_allclose(left[0]["frob"], ref.frob(), rtol=1e-10)

@@ -71,3 +71,15 @@ def test_batch_member_deterministic():
     b = gen.random_batch_member(3)
     assert a.n == b.n and np.array_equal(a.val, b.val)
     assert 500 <= a.n <= 60000
+
+
+def test_transpose_swaps_formats_without_arithmetic():
+    from paper_1503_04500_gb300 import rsai
+
+    A = gen.powerlaw(500, seed=3, dmax=30)
+    T = rsai.transpose(A)
+    np.testing.assert_array_equal(T.to_dense(), A.to_dense().T)
+    np.testing.assert_array_equal(T.cval, T.val[T.csc_to_csr])  # the map still pairs the two copies
+    TT = rsai.transpose(T)
+    for f in ("row_ptr", "col_idx", "val", "col_ptr", "row_idx", "cval", "csc_to_csr"):
+        np.testing.assert_array_equal(getattr(TT, f), getattr(A, f))
