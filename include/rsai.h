@@ -362,7 +362,9 @@ rsai_status rsai_spmv_grad_values(const rsai_csr *A, const double *gy, const dou
  * The setting is process-wide and applies to handles created afterwards (a
  * handle frees with the allocator it was created with), to the temporaries of
  * rsai_refit and to the workspace of rsai_bicgstab.  alloc = release = NULL
- * restores cudaMallocAsync / cudaFreeAsync.  Not thread-safe against builds
+ * restores the default: a stream-ordered pool of the library's own on each
+ * device (cudaMallocFromPoolAsync / cudaFreeAsync), which keeps up to 2 GiB of
+ * freed handle memory mapped for the next handle.  Not thread-safe against builds
  * running on other threads.  Errors: INVALID_ARG when exactly one of the two
  * is NULL.
  */

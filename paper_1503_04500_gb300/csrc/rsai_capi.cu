@@ -4,13 +4,14 @@
 // the per-column outputs, the result pool, the overflow queues of the size
 // bins, M in CSC and CSR, and the CUDA graph of the build sequence.  All device
 // memory is taken on the caller's stream, from the allocator installed with
-// rsai_set_allocator when the handle was created, else with cudaMallocAsync /
-// cudaFreeAsync; nothing is allocated by the build sequence itself, so
+// rsai_set_allocator when the handle was created, else from the library's own
+// stream-ordered pool; nothing is allocated by the build sequence itself, so
 // rsai_rebuild can replay it as one CUDA graph.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -106,10 +107,41 @@ double *dword(const rsai_handle *h, int at) { return reinterpret_cast<double *>(
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? RSAI_OK : RSAI_ERR_CUDA; }
 
+// The library's own stream-ordered pool on the current device.  Up to
+// kPoolKeep bytes that handles give back stay mapped in it, so that building
+// and freeing handles repeatedly does not map and unmap device memory each
+// time; the application's default pool is left as it is.
+constexpr uint64_t kPoolKeep = 2ull << 30;
+
+cudaMemPool_t library_pool() {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = kPoolKeep;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = pool;
+    }
+    return pools[dev];
+}
+
 void *raw_alloc(const Allocator &a, size_t bytes, cudaStream_t st) {
     void *p = nullptr;
     if (a.alloc) return a.alloc(bytes, (void *)st, a.ctx);
-    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+    cudaMemPool_t pool = library_pool();
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, st) : cudaMallocAsync(&p, bytes, st);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
@@ -265,7 +297,7 @@ void free_all(rsai_handle *h) {
     cudaDeviceSynchronize();
     for (auto &a : h->allocs) {
         if (h->allocator.release) h->allocator.release(a.first, a.second, nullptr, h->allocator.ctx);
-        else cudaFree(a.first);
+        else cudaFreeAsync(a.first, nullptr);  // the device is idle: returned to the pool at once
     }
     h->allocs.clear();
 }
