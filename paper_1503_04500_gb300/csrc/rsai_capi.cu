@@ -293,13 +293,18 @@ void free_all(rsai_handle *h) {
     if (!h) return;
     if (h->graph) cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
-    // the caller's stream may be gone by now: wait for the device, then free
+    // the caller's stream may be gone by now: wait for the handle's device,
+    // then free there (the current device is restored)
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != h->device) cudaSetDevice(h->device);
     cudaDeviceSynchronize();
     for (auto &a : h->allocs) {
         if (h->allocator.release) h->allocator.release(a.first, a.second, nullptr, h->allocator.ctx);
         else cudaFreeAsync(a.first, nullptr);  // the device is idle: returned to the pool at once
     }
     h->allocs.clear();
+    if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
 }
 
 int check_csr_host(const rsai_csr *A) {
