@@ -5,7 +5,8 @@ shape (warps per CTA of the warp bin, resident CTAs per SM, the largest |J|
 given to the register-resident warp QR), keeps the fastest and caches it in a
 JSON file keyed by GPU name, precision and a coarse signature of the problem
 (n and nnz/n rounded to powers of two), so later builds of similar problems
-start from the cached shape.  Results do not depend on the shape.
+start from the cached shape.  The CTA shapes leave results bit-identical;
+the register-QR threshold changes only the rounding of the LS solutions.
 """
 from __future__ import annotations
 

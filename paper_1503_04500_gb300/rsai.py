@@ -337,7 +337,8 @@ class Handle:
         return t.as_dict()
 
     def set_tuning(self, **kw):
-        """rsai_set_tuning: launch shapes of the bins (speed only, identical results)."""
+        """rsai_set_tuning: launch shapes of the bins (CTA shapes: identical results; the
+        register-QR threshold: the same solutions up to rounding)."""
         t = Tuning(**{**self.tuning(), **kw})
         _check(load().rsai_set_tuning(self._h, ctypes.byref(t)), "rsai_set_tuning")
 
