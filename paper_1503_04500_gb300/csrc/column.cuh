@@ -291,16 +291,22 @@ __device__ __forceinline__ void wy_apply(const Team &team, const T *V, int qq, i
         for (int x = 0; x < kCols; ++x)
 #pragma unroll
             for (int u = 0; u < kPanel; ++u) wv[x][u] = T(0);
-        for (int r = lane; r < qq; r += 32) {
-            T cr[kCols];
+        // two rows per pass (r and r + 32), their loads issued before any use
+        for (int r = lane; r < qq; r += 64) {
+            const bool two = r + 32 < qq;
+            T cr[kCols], cr2[kCols];
 #pragma unroll
-            for (int x = 0; x < kCols; ++x) cr[x] = tc[x] ? tc[x][r] : T(0);
+            for (int x = 0; x < kCols; ++x) {
+                cr[x] = tc[x] ? tc[x][r] : T(0);
+                cr2[x] = (tc[x] && two) ? tc[x][r + 32] : T(0);
+            }
 #pragma unroll
             for (int u = 0; u < kPanel; ++u) {
                 if (u < nb) {
                     const T v = V[(int64_t)u * qq + r];
+                    const T v2 = two ? V[(int64_t)u * qq + r + 32] : T(0);
 #pragma unroll
-                    for (int x = 0; x < kCols; ++x) wv[x][u] += v * cr[x];
+                    for (int x = 0; x < kCols; ++x) wv[x][u] += v * cr[x] + v2 * cr2[x];
                 }
             }
         }
@@ -322,21 +328,33 @@ __device__ __forceinline__ void wy_apply(const Team &team, const T *V, int qq, i
                 wv[x][u] = acc;
             }
         }
-        for (int r = lane; r < qq; r += 32) {
-            T acc[kCols];
+        for (int r = lane; r < qq; r += 64) {
+            const bool two = r + 32 < qq;
+            T acc[kCols], acc2[kCols];
 #pragma unroll
-            for (int x = 0; x < kCols; ++x) acc[x] = tc[x] ? tc[x][r] : T(0);
+            for (int x = 0; x < kCols; ++x) {
+                acc[x] = tc[x] ? tc[x][r] : T(0);
+                acc2[x] = (tc[x] && two) ? tc[x][r + 32] : T(0);
+            }
 #pragma unroll
             for (int u = 0; u < kPanel; ++u) {
                 if (u < nb) {
                     const T v = V[(int64_t)u * qq + r];
+                    const T v2 = two ? V[(int64_t)u * qq + r + 32] : T(0);
 #pragma unroll
-                    for (int x = 0; x < kCols; ++x) acc[x] -= v * wv[x][u];
+                    for (int x = 0; x < kCols; ++x) {
+                        acc[x] -= v * wv[x][u];
+                        acc2[x] -= v2 * wv[x][u];
+                    }
                 }
             }
 #pragma unroll
-            for (int x = 0; x < kCols; ++x)
-                if (tc[x]) tc[x][r] = acc[x];
+            for (int x = 0; x < kCols; ++x) {
+                if (tc[x]) {
+                    tc[x][r] = acc[x];
+                    if (two) tc[x][r + 32] = acc2[x];
+                }
+            }
         }
     }
     team.sync();
