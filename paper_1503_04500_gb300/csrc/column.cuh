@@ -291,22 +291,27 @@ __device__ __forceinline__ void wy_apply(const Team &team, const T *V, int qq, i
         for (int x = 0; x < kCols; ++x)
 #pragma unroll
             for (int u = 0; u < kPanel; ++u) wv[x][u] = T(0);
-        // two rows per pass (r and r + 32), their loads issued before any use
-        for (int r = lane; r < qq; r += 64) {
-            const bool two = r + 32 < qq;
-            T cr[kCols], cr2[kCols];
+        // kRows rows per pass (r, r + 32, ...), their loads issued before any use
+        constexpr int kRows = 4;
+        for (int r = lane; r < qq; r += 32 * kRows) {
+            T cr[kRows][kCols];
 #pragma unroll
-            for (int x = 0; x < kCols; ++x) {
-                cr[x] = tc[x] ? tc[x][r] : T(0);
-                cr2[x] = (tc[x] && two) ? tc[x][r + 32] : T(0);
-            }
+            for (int y = 0; y < kRows; ++y)
+#pragma unroll
+                for (int x = 0; x < kCols; ++x) cr[y][x] = (tc[x] && r + 32 * y < qq) ? tc[x][r + 32 * y] : T(0);
 #pragma unroll
             for (int u = 0; u < kPanel; ++u) {
                 if (u < nb) {
-                    const T v = V[(int64_t)u * qq + r];
-                    const T v2 = two ? V[(int64_t)u * qq + r + 32] : T(0);
+                    T v[kRows];
 #pragma unroll
-                    for (int x = 0; x < kCols; ++x) wv[x][u] += v * cr[x] + v2 * cr2[x];
+                    for (int y = 0; y < kRows; ++y) v[y] = (r + 32 * y < qq) ? V[(int64_t)u * qq + r + 32 * y] : T(0);
+#pragma unroll
+                    for (int x = 0; x < kCols; ++x) {
+                        T sacc = 0;
+#pragma unroll
+                        for (int y = 0; y < kRows; ++y) sacc += v[y] * cr[y][x];
+                        wv[x][u] += sacc;
+                    }
                 }
             }
         }
@@ -328,33 +333,28 @@ __device__ __forceinline__ void wy_apply(const Team &team, const T *V, int qq, i
                 wv[x][u] = acc;
             }
         }
-        for (int r = lane; r < qq; r += 64) {
-            const bool two = r + 32 < qq;
-            T acc[kCols], acc2[kCols];
+        for (int r = lane; r < qq; r += 32 * kRows) {
+            T acc[kRows][kCols];
 #pragma unroll
-            for (int x = 0; x < kCols; ++x) {
-                acc[x] = tc[x] ? tc[x][r] : T(0);
-                acc2[x] = (tc[x] && two) ? tc[x][r + 32] : T(0);
-            }
+            for (int y = 0; y < kRows; ++y)
+#pragma unroll
+                for (int x = 0; x < kCols; ++x) acc[y][x] = (tc[x] && r + 32 * y < qq) ? tc[x][r + 32 * y] : T(0);
 #pragma unroll
             for (int u = 0; u < kPanel; ++u) {
                 if (u < nb) {
-                    const T v = V[(int64_t)u * qq + r];
-                    const T v2 = two ? V[(int64_t)u * qq + r + 32] : T(0);
 #pragma unroll
-                    for (int x = 0; x < kCols; ++x) {
-                        acc[x] -= v * wv[x][u];
-                        acc2[x] -= v2 * wv[x][u];
+                    for (int y = 0; y < kRows; ++y) {
+                        const T v = (r + 32 * y < qq) ? V[(int64_t)u * qq + r + 32 * y] : T(0);
+#pragma unroll
+                        for (int x = 0; x < kCols; ++x) acc[y][x] -= v * wv[x][u];
                     }
                 }
             }
 #pragma unroll
-            for (int x = 0; x < kCols; ++x) {
-                if (tc[x]) {
-                    tc[x][r] = acc[x];
-                    if (two) tc[x][r + 32] = acc2[x];
-                }
-            }
+            for (int y = 0; y < kRows; ++y)
+#pragma unroll
+                for (int x = 0; x < kCols; ++x)
+                    if (tc[x] && r + 32 * y < qq) tc[x][r + 32 * y] = acc[y][x];
         }
     }
     team.sync();
