@@ -17,7 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librsai.so")
-SOURCES = ["rsai_capi.cu", "build_kernels.cu", "apply_kernels.cu", "peak_kernels.cu", "noalloc_bicgstab.cu"]
+SOURCES = ["rsai_capi.cu", "build_kernels.cu", "setup_kernels.cu", "apply_kernels.cu", "peak_kernels.cu",
+           "noalloc_bicgstab.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
