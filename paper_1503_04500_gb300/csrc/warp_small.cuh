@@ -26,6 +26,15 @@ template <typename T> __device__ __forceinline__ T warp_sum_t(T x) {
 
 __host__ __device__ constexpr int ilog2_c(int m) { return m <= 1 ? 0 : 1 + ilog2_c(m >> 1); }
 
+// Square root and quotient of the register QR's Householder steps.  In FP32
+// (the factorization that the FP64 refinement step corrects) the hardware
+// approximations (rsqrtf, __fdividef, about 2 ulp) replace the correctly
+// rounded sequences; in FP64 they stay exact.
+__device__ __forceinline__ float qr_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+__device__ __forceinline__ double qr_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float qr_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double qr_div(double a, double b) { return a / b; }
+
 // All-reduce of M values (M a power of two <= 32) over the warp: on entry
 // lane l holds partial sums x[0..M); on exit every lane holds the M totals.
 // Reduce-scatter by recursive halving (at the level with xor distance o the
@@ -120,12 +129,12 @@ __device__ __noinline__ int warp_qr_small(T *B, int q, int p, T *rhs, T *vhead, 
             T v1 = b1[j];
             const T sigma = warp_sum_t(v0 * v0 + v1 * v1);
             const T x0 = __shfl_sync(0xffffffffu, b0[j], j);
-            const T nrm = sqrt(sigma);
+            const T nrm = qr_sqrt(sigma);
             const T alpha = (x0 >= T(0)) ? -nrm : nrm;
             const T vh = x0 - alpha;
             const T vv = sigma - x0 * x0 + vh * vh;
             if (lane == j) v0 = vh;
-            const T two_over = (vv > T(0)) ? T(2) / vv : T(0);
+            const T two_over = (vv > T(0)) ? qr_div(T(2), vv) : T(0);
             {
                 // j is a constant in each unrolled step, so one branch survives
                 const int m = kSmallP - j;
