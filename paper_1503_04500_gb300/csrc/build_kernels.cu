@@ -199,12 +199,25 @@ size_t work_bytes(const Caps &c) { return Work<T>::bytes(c); }
 template size_t work_bytes<float>(const Caps &);
 template size_t work_bytes<double>(const Caps &);
 
+// Lets `fn` take up to the device's opt-in shared memory per block, less its
+// static shared memory.  The limit is raised to that largest value instead of
+// to each launch's size, so that every launch recorded in a CUDA graph stays
+// within the function's limit whatever was launched (or planned) after it.
+template <typename F> static void allow_full_smem(F fn) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, fn);  // static + dynamic must not exceed the opt-in limit
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 template <typename T, int MODE>
 static cudaError_t launch_warp_t(int grid, int warps, const DevA &A, const DevParams &P, const Caps &cap,
                                  const ColQueue &Q, const ColOut &O, const Frozen &F, unsigned long long *gctr,
                                  bool last, cudaStream_t st) {
     size_t smem = warp_bin_smem<T>(cap, warps);
-    cudaFuncSetAttribute(k_bin_warp<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_full_smem(k_bin_warp<T, MODE>);
     k_bin_warp<T, MODE><<<grid, warps * 32, smem, st>>>(A, P, cap, Q, O, F, gctr, last ? 1 : 0);
     return cudaGetLastError();
 }
@@ -214,7 +227,7 @@ static cudaError_t launch_block_t(int grid, const DevA &A, const DevParams &P, c
                                   const ColOut &O, const Frozen &F, unsigned long long *gctr, bool last, char *gwork,
                                   size_t gstride, int bin, cudaStream_t st) {
     size_t smem = gwork ? (size_t)cap.stage_bytes : Work<T>::bytes(cap);
-    cudaFuncSetAttribute(k_bin_block<T, kBlockThreads, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_full_smem(k_bin_block<T, kBlockThreads, MODE>);
     k_bin_block<T, kBlockThreads, MODE><<<grid, kBlockThreads, smem, st>>>(A, P, cap, Q, O, F, gctr, last ? 1 : 0,
                                                                           gwork, gstride, bin);
     return cudaGetLastError();
@@ -253,10 +266,10 @@ int occupancy_bin_warp(bool fp32, int warps, const Caps &cap) {
     int nb = 0;
     size_t smem = fp32 ? warp_bin_smem<float>(cap, warps) : warp_bin_smem<double>(cap, warps);
     if (fp32) {
-        cudaFuncSetAttribute(k_bin_warp<float, MODE_BUILD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_full_smem(k_bin_warp<float, MODE_BUILD>);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bin_warp<float, MODE_BUILD>, warps * 32, smem);
     } else {
-        cudaFuncSetAttribute(k_bin_warp<double, MODE_BUILD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_full_smem(k_bin_warp<double, MODE_BUILD>);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bin_warp<double, MODE_BUILD>, warps * 32, smem);
     }
     return nb;
@@ -266,13 +279,11 @@ int occupancy_bin_block(bool fp32, const Caps &cap, bool global_work) {
     int nb = 0;
     size_t smem = global_work ? 0 : (fp32 ? Work<float>::bytes(cap) : Work<double>::bytes(cap));
     if (fp32) {
-        cudaFuncSetAttribute(k_bin_block<float, kBlockThreads, MODE_BUILD>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_full_smem(k_bin_block<float, kBlockThreads, MODE_BUILD>);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bin_block<float, kBlockThreads, MODE_BUILD>,
                                                       kBlockThreads, smem);
     } else {
-        cudaFuncSetAttribute(k_bin_block<double, kBlockThreads, MODE_BUILD>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_full_smem(k_bin_block<double, kBlockThreads, MODE_BUILD>);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bin_block<double, kBlockThreads, MODE_BUILD>,
                                                       kBlockThreads, smem);
     }
