@@ -12,7 +12,9 @@
  *
  * What it computes, per column k (Section 2 Eq. 2.2-2.4, Section 3 Algorithm 1,
  * Section 4 Eq. 4.3):
- *   J = {k}, R = {}, l = 0                           (Algorithm 1 step 1)
+ *   J = J0(k), R = {}, l = 0                         (Algorithm 1 step 1)
+ *     J0(k) = {k} (the pattern of I, the paper's usual choice) or the
+ *     pattern of column k of A (init_mode 1)
  *   Solve(J); Drop(J); r = A m - e_k; rho = ||r||    (step 2 + Eq. 4.3)
  *   while rho > eps and l < l_max                    (step 3)
  *     L = {i in S : |r_i| > band};  Cand = L \ R     (step 4, Eq. 3.2)
@@ -73,7 +75,7 @@ typedef struct {
 } omat;
 
 typedef struct {
-    int32_t c, l_max, drop_mode;
+    int32_t c, l_max, drop_mode, init_mode;  /* init_mode: 0 = pattern of I, 1 = pattern of A */
     double eps, tol, tie_band, norm1;
 } oparams;
 
@@ -298,6 +300,17 @@ static void rsai_column(const omat *A, const oparams *P, int64_t k, ocol *out, o
     int64_t qmax = 0;
     double qr_flops = 0.0, res_flops = 0.0, bytes = 0.0, rho = 0.0, nnzJ = 0.0;
     J[0] = (int32_t)k;
+    if (P->init_mode == 1) {
+        /* Algorithm 1 step 1 with the initial pattern of A: J = rows of A(:,k) */
+        int64_t len = A->col_ptr[k + 1] - A->col_ptr[k];
+        if (len > 0) {
+            J = grow(J, &capJ, len, sizeof(int32_t));
+            m = realloc(m, sizeof(double) * (size_t)capJ);
+            for (int64_t e = 0; e < len; ++e) J[e] = A->row_idx[A->col_ptr[k] + e];
+            p = (int)len;
+            pmax = p;
+        }
+    }
 
     /* bytes of a column of A each time it enters J */
 #define NOTE_COLUMN(j) (bytes += 12.0 * (double)(A->col_ptr[(j) + 1] - A->col_ptr[(j)]) + 16.0)
@@ -333,7 +346,7 @@ static void rsai_column(const omat *A, const oparams *P, int64_t k, ocol *out, o
         }                                                                             \
     } while (0)
 
-    NOTE_COLUMN((int32_t)k);
+    for (int c = 0; c < p; ++c) NOTE_COLUMN(J[c]);
     SOLVE(0);
     DROP();
     int64_t s = residual(A, k, J, p, m, w, &rho, &nnzJ);
@@ -433,9 +446,9 @@ static void rsai_column(const omat *A, const oparams *P, int64_t k, ocol *out, o
 void *ro_build(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const double *val,
                const int64_t *col_ptr, const int32_t *row_idx, const double *cval,
                int32_t c, int32_t l_max, double eps, int32_t drop_mode, double tol, double tie_band,
-               const int64_t *cols, int64_t ncols, int32_t nthreads) {
+               const int64_t *cols, int64_t ncols, int32_t nthreads, int32_t init_mode) {
     omat A = {n, row_ptr, col_idx, val, col_ptr, row_idx, cval};
-    oparams P = {c, l_max, drop_mode, eps, tol, tie_band, ro_norm1(n, col_ptr, cval)};
+    oparams P = {c, l_max, drop_mode, init_mode, eps, tol, tie_band, ro_norm1(n, col_ptr, cval)};
     oresult *res = calloc(1, sizeof(oresult));
     if (!cols) ncols = n;
     res->ncols = ncols;

@@ -48,7 +48,7 @@ def _load():
             lib.ro_build.restype = ctypes.c_void_p
             lib.ro_build.argtypes = mat + [ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                            ctypes.c_int32, ctypes.c_double, ctypes.c_double,
-                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]
+                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]
             lib.ro_nnz.restype = ctypes.c_int64
             lib.ro_nnz.argtypes = [ctypes.c_void_p]
             lib.ro_export.restype = None
@@ -118,8 +118,11 @@ class OracleM:
         return np.cumsum(row_ptr), colk[order].astype(np.int32), self.vals[order]
 
 
-def build(A, c=3, l_max=10, eps=0.3, drop="fixed", tol=1e-3, tie_band=1e-12, cols=None, threads=0) -> OracleM:
-    """RSAI(tol) columns of M (Algorithm 1 + Eq. 4.3) for the given columns."""
+def build(A, c=3, l_max=10, eps=0.3, drop="fixed", tol=1e-3, tie_band=1e-12, cols=None, threads=0,
+          init="identity") -> OracleM:
+    """RSAI(tol) columns of M (Algorithm 1 + Eq. 4.3) for the given columns.
+    ``init``: the initial pattern J_k^(0) of Algorithm 1 step 1, "identity" ({k})
+    or "A" (the rows of column k of A)."""
     lib = _load()
     args = _mat(A)
     mode = _DROP[drop] if isinstance(drop, str) else int(drop)
@@ -130,7 +133,7 @@ def build(A, c=3, l_max=10, eps=0.3, drop="fixed", tol=1e-3, tie_band=1e-12, col
         colsa = np.ascontiguousarray(cols, dtype=np.int64)
         ptr = colsa.ctypes.data_as(ctypes.c_void_p)
     h = lib.ro_build(*args, int(c), int(l_max), float(eps), mode, float(tol), float(tie_band),
-                     ptr, int(len(colsa)), int(threads))
+                     ptr, int(len(colsa)), int(threads), {"identity": 0, "A": 1}[init])
     try:
         nnz = lib.ro_nnz(h)
         nc = len(colsa)

@@ -241,3 +241,27 @@ def test_golden_exact_small():
             assert list(J) == col["J"]
             np.testing.assert_allclose(v, [float(Fraction(x)) for x in col["m"]], rtol=1e-12, atol=1e-15)
             assert M.loops[t] == col["loops"]
+
+
+def test_initial_pattern_of_A_is_the_least_squares_solution_on_it(c1):
+    """Algorithm 1 step 1 with J_k^(0) = rows of column k of A and no loop
+    (l_max = 0, no dropping): every column is the LS minimiser of
+    ||A(:,J) m - e_k|| on that pattern, which NumPy's lstsq gives directly."""
+    A = gen.convdiff2d(10, (7.0, -3.0))
+    M = oracle.build(A, c=3, l_max=0, eps=1e-12, drop="none", init="A")
+    D = A.to_dense()
+    for t, k in enumerate(M.cols):
+        J, v = M.column(t)
+        expect_J = np.sort(A.row_idx[A.col_ptr[k]:A.col_ptr[k + 1]])
+        np.testing.assert_array_equal(J, expect_J)
+        e = np.zeros(A.n)
+        e[k] = 1.0
+        x, *_ = np.linalg.lstsq(D[:, J], e, rcond=None)
+        np.testing.assert_allclose(v, x, rtol=1e-12, atol=1e-14 * np.abs(x).max())
+        np.testing.assert_allclose(M.rho[t], np.linalg.norm(D[:, J] @ x - e), rtol=1e-12)
+        assert M.loops[t] == 0
+    # with loops, the initial pattern is kept unless a drop removes it: J^(0) is a subset of J
+    M2 = oracle.build(A, c=3, l_max=5, eps=0.1, drop="none", init="A")
+    for t, k in enumerate(M2.cols):
+        J, _ = M2.column(t)
+        assert set(A.row_idx[A.col_ptr[k]:A.col_ptr[k + 1]]) <= set(J)
