@@ -90,7 +90,11 @@ enum {
 
 /* Flags */
 enum {
-    RSAI_FLAG_CHECKED = 1u /* extra device-side bounds checks (status, never a trap) */
+    RSAI_FLAG_CHECKED = 1u,       /* accepted, no effect: the input checks (ranges, sortedness, the
+                                     CSR/CSC pairing) always run and report status codes */
+    RSAI_FLAG_INIT_PATTERN_A = 2u /* initial pattern J_k^(0) = rows of column k of A instead of {k}
+                                     (Algorithm 1 step 1 leaves it to the user; Section 3 suggests
+                                     that of I, the default, when A has a nonzero diagonal) */
 };
 
 /* Parameters of RSAI(tol) (Algorithm 1 step 1; Section 3 defaults c ~ 3,

@@ -1287,7 +1287,19 @@ template <class Team, typename T> struct Column {
         c_solves = c_drops = c_pmax = c_qmax = 0;
         if (me == 0) w.J[0] = k;
         team.sync();
-        c_bytes += 12 * (A.col_ptr[k + 1] - A.col_ptr[k]) + 16;
+        if (P.init_a) {
+            // Algorithm 1 step 1 with the initial pattern of A: J = rows of A(:,k)
+            // (ascending in the CSC), solved by the general path below
+            const int64_t e0 = A.col_ptr[k];
+            const int len = (int)(A.col_ptr[k + 1] - e0);
+            if (len > cap.pcap) return COL_OVERFLOW;
+            for (int c = me; c < len; c += Team::SIZE) w.J[c] = A.row_idx[e0 + c];
+            p = len;
+            team.sync();
+            note_bytes_columns(0, p, w.J);
+        } else {
+            c_bytes += 12 * (A.col_ptr[k + 1] - A.col_ptr[k]) + 16;
+        }
         // One solve site: the first pass of every round solves on the new J
         // (appended to the last factor after the first round), the second
         // re-solves after a drop (Eq. 4.3); then the residual (Eq. 2.4).
@@ -1295,8 +1307,8 @@ template <class Team, typename T> struct Column {
         for (;;) {
             for (int pass = 0; pass < 2; ++pass) {
                 if (first) {
-                    if (!initial_solve()) return COL_OVERFLOW;
                     first = false;
+                    if (P.init_a ? !solve(false) : !initial_solve()) return COL_OVERFLOW;
                 } else if (!solve(append)) {
                     return COL_OVERFLOW;
                 }

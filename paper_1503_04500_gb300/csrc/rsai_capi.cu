@@ -189,6 +189,7 @@ DevParams dev_params(const rsai_handle *h) {
     P.l_max = h->params.l_max;
     P.drop_mode = h->params.drop_mode;
     P.precision = h->params.precision;
+    P.init_a = (h->params.flags & RSAI_FLAG_INIT_PATTERN_A) ? 1 : 0;
     P.eps = h->params.eps;
     P.tol = h->params.tol;
     P.tie_band = h->params.tie_band;
@@ -403,6 +404,7 @@ rsai_status rsai_params_check(const rsai_params *p) {
     if (!(p->tol >= 0.0) || !std::isfinite(p->tol)) return RSAI_ERR_INVALID_ARG;
     if (p->precision != RSAI_FP64 && p->precision != RSAI_FP32_REFINE) return RSAI_ERR_INVALID_ARG;
     if (!(p->tie_band >= 0.0) || !(p->tie_band < 1.0)) return RSAI_ERR_INVALID_ARG;
+    if (p->flags & ~(uint32_t)(RSAI_FLAG_CHECKED | RSAI_FLAG_INIT_PATTERN_A)) return RSAI_ERR_INVALID_ARG;
     return RSAI_OK;
 }
 

@@ -22,6 +22,7 @@ STATUS_NAMES = {
     7: "CUDA", 8: "TIMEOUT", 9: "WORKSPACE", 10: "BREAKDOWN", 11: "NOT_CONVERGED", 12: "NO_DEVICE",
     13: "TOO_LARGE",
 }
+FLAG_INIT_PATTERN_A = 2  # RSAI_FLAG_INIT_PATTERN_A
 DROP = {"none": 0, "adaptive": 1, "fixed": 2}
 PRECISION = {"fp64": 0, "fp32_refine": 1}
 COL_CONVERGED, COL_RANK, COL_NONFINITE, COL_FAILED = 1, 2, 4, 8
@@ -211,6 +212,9 @@ def default_params(**kw) -> Params:
             p.drop_mode = DROP[v] if isinstance(v, str) else int(v)
         elif k == "precision":
             p.precision = PRECISION[v] if isinstance(v, str) else int(v)
+        elif k == "init":
+            # initial pattern J_k^(0) (Algorithm 1 step 1): "identity" ({k}) or "A" (rows of A(:,k))
+            p.flags = (p.flags & ~FLAG_INIT_PATTERN_A) | (FLAG_INIT_PATTERN_A if v == "A" else 0)
         else:
             setattr(p, k, v)
     return p
@@ -384,11 +388,12 @@ class Handle:
 
 
 def build(A, c=3, l_max=10, eps=0.3, drop="fixed", tol=1e-3, precision="fp64", tie_band=1e-12, stream=None,
-          allow_failed=False) -> Handle:
+          allow_failed=False, init="identity") -> Handle:
     """rsai_build on a DeviceMatrix (device tensors) or a SparseMatrix-like
     object with numpy arrays (then the library copies from host memory)."""
     lib = load()
-    params = default_params(c=c, l_max=l_max, eps=eps, drop=drop, tol=tol, precision=precision, tie_band=tie_band)
+    params = default_params(c=c, l_max=l_max, eps=eps, drop=drop, tol=tol, precision=precision, tie_band=tie_band,
+                            init=init)
     if isinstance(A, DeviceMatrix):
         csr, csc, keep = A.csr(), A.csc(), None
     else:

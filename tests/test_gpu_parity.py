@@ -395,3 +395,25 @@ def test_sweep_rows_and_monotone_residual():
     A = gen.convdiff2d(12, (20.0, 20.0))
     ref = oracle.build(rsai.transpose(A), c=2, l_max=6, eps=0.2, drop="none")
     np.testing.assert_allclose(left[0]["frob"], ref.frob(), rtol=1e-10)
+
+
+@pytest.mark.parametrize("drop", ["fixed", "none"])
+def test_initial_pattern_of_A(c1, drop):
+    """Algorithm 1 step 1 with J_k^(0) = rows of A(:,k) (RSAI_FLAG_INIT_PATTERN_A):
+    FP64 patterns bit-identical to the oracle's, values to 1e-10, the same
+    work counters; FP32+refine within the FP32 tolerances."""
+    h, dA, res, rho, loops, flags, st = gpu_M(c1, drop=drop, precision="fp64", init="A", **PARAMS_C1)
+    ref = oracle.build(c1, drop=drop, init="A", **PARAMS_C1)
+    assert_fp64_parity(c1, ref, res, rho, loops, flags, st)
+    assert st["qr_flops"] == ref.counters[:, 0].sum()
+    assert st["bytes"] == ref.counters[:, 2].sum()
+    assert st["solves"] == ref.counters[:, 3].sum()
+    assert st["drops"] == ref.counters[:, 4].sum()
+    assert st["p_max"] == ref.counters[:, 5].max()
+    plain = oracle.build(c1, drop=drop, **PARAMS_C1)
+    assert ref.nnz != plain.nnz  # the option changes the result
+    h2, _, res2, rho2, *_ = gpu_M(c1, drop=drop, precision="fp32_refine", init="A", **PARAMS_C1)
+    cp, rows, _ = csc_from_csr(*res2, c1.n)
+    same = np.array([np.array_equal(rows[cp[k]:cp[k + 1]], ref.column(k)[0]) for k in range(c1.n)])
+    assert same.mean() >= 0.99
+    np.testing.assert_allclose(rho2[same], ref.rho[same], rtol=1e-5)
