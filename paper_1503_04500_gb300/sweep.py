@@ -43,7 +43,7 @@ def _ints(s: str):
 
 
 def run(workload="convdiff2d", size=20, seed=1503, eps=(0.3,), c=(3,), lmax=(10,), drop="fixed", tol=1e-3,
-        precision="fp64", side="right", rebuilds=5, solve=True):
+        precision="fp64", side="right", rebuilds=5, solve=True, init="identity"):
     """Yield one result dict per (eps, c, l_max) setting."""
     import torch
 
@@ -52,7 +52,7 @@ def run(workload="convdiff2d", size=20, seed=1503, eps=(0.3,), c=(3,), lmax=(10,
     b = torch.as_tensor(inputs.ones_rhs(A), device="cuda")
     st = torch.cuda.current_stream()
     for e, cc, lm in itertools.product(eps, c, lmax):
-        kw = dict(c=cc, l_max=lm, eps=e, drop=drop, tol=tol, precision=precision)
+        kw = dict(c=cc, l_max=lm, eps=e, drop=drop, tol=tol, precision=precision, init=init)
         t0 = time.perf_counter()
         h = rsai.build_left(dA, **kw) if side == "left" else rsai.build(dA, **kw)
         torch.cuda.synchronize()
@@ -68,7 +68,8 @@ def run(workload="convdiff2d", size=20, seed=1503, eps=(0.3,), c=(3,), lmax=(10,
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
         s = h.stats()
-        out = {"workload": workload, "n": A.n, "nnz_A": A.nnz, "side": side, "precision": precision, "eps": e,
+        out = {"workload": workload, "n": A.n, "nnz_A": A.nnz, "side": side, "init": init, "precision": precision,
+               "eps": e,
                "c": cc, "l_max": lm, "drop": drop, "tol": tol, "spar": s["nnz_M"] / A.nnz, "frob": s["frob"],
                "n_c": s["n_c"], "p_max": s["p_max"], "q_max": s["q_max"], "cols_bin": s["cols_bin"],
                "build_ms": statistics.median(times) if times else None, "first_build_s": first_s,
@@ -98,9 +99,11 @@ def main(argv=None):
     ap.add_argument("--side", default="right", choices=["right", "left"])
     ap.add_argument("--rebuilds", type=int, default=5)
     ap.add_argument("--no-solve", dest="solve", action="store_false")
+    ap.add_argument("--init", default="identity", choices=["identity", "A"],
+                    help="initial pattern J_k^(0): {k} or the rows of column k of A")
     a = ap.parse_args(argv)
     for row in run(a.workload, a.size, a.seed, _floats(a.eps), _ints(a.c), _ints(a.lmax), a.drop, a.tol,
-                   a.precision, a.side, a.rebuilds, a.solve):
+                   a.precision, a.side, a.rebuilds, a.solve, a.init):
         print(json.dumps(row), flush=True)
 
 
