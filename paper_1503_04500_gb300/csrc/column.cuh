@@ -527,6 +527,27 @@ __device__ __noinline__ void qr_update_apply(Team team, T *B, int q, int p, int 
     }
 }
 
+// J = rows of A(:,k), ascending as the CSC keeps them; returns |J|, or -1 if
+// it exceeds pcap, and in *bytes the algorithmic bytes of J's columns (12 per
+// nonzero + 16 each).  Kept out of line: only the initial pattern of A uses it.
+template <class Team>
+__device__ __noinline__ int pattern_of_column(Team team, const int64_t *col_ptr, const int32_t *row_idx, int32_t k,
+                                              int pcap, int32_t *J, long long *bytes) {
+    const int me = team.rank();
+    const int64_t e0 = col_ptr[k];
+    const int len = (int)(col_ptr[k + 1] - e0);
+    if (len > pcap) return -1;
+    long long b = 0;
+    for (int c = me; c < len; c += Team::SIZE) {
+        const int32_t j = row_idx[e0 + c];
+        J[c] = j;
+        b += 12 * (col_ptr[j + 1] - col_ptr[j]) + 16;
+    }
+    *bytes = team.sum(b);
+    team.sync();
+    return len;
+}
+
 template <class Team, typename T> struct Column {
     const Team &team;
     const DevA &A;
@@ -1288,15 +1309,13 @@ template <class Team, typename T> struct Column {
         if (me == 0) w.J[0] = k;
         team.sync();
         if (P.init_a) {
-            // Algorithm 1 step 1 with the initial pattern of A: J = rows of A(:,k)
-            // (ascending in the CSC), solved by the general path below
-            const int64_t e0 = A.col_ptr[k];
-            const int len = (int)(A.col_ptr[k + 1] - e0);
-            if (len > cap.pcap) return COL_OVERFLOW;
-            for (int c = me; c < len; c += Team::SIZE) w.J[c] = A.row_idx[e0 + c];
+            // Algorithm 1 step 1 with the initial pattern of A, solved by the
+            // general path below
+            long long b = 0;
+            const int len = pattern_of_column(team, A.col_ptr, A.row_idx, k, cap.pcap, w.J, &b);
+            if (len < 0) return COL_OVERFLOW;
             p = len;
-            team.sync();
-            note_bytes_columns(0, p, w.J);
+            c_bytes += b;
         } else {
             c_bytes += 12 * (A.col_ptr[k + 1] - A.col_ptr[k]) + 16;
         }
@@ -1306,12 +1325,14 @@ template <class Team, typename T> struct Column {
         bool append = false, first = true;
         for (;;) {
             for (int pass = 0; pass < 2; ++pass) {
-                if (first) {
-                    first = false;
-                    if (P.init_a ? !solve(false) : !initial_solve()) return COL_OVERFLOW;
+                // one call site of solve() (it is large and inlined): the
+                // closed form covers the first solve of J = {k} only
+                if (first && !P.init_a) {
+                    if (!initial_solve()) return COL_OVERFLOW;
                 } else if (!solve(append)) {
                     return COL_OVERFLOW;
                 }
+                first = false;
                 append = false;
                 if (pass == 1 || !drop()) break;
             }
