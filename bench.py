@@ -34,8 +34,9 @@ sys.path.insert(0, ROOT)
 PARAMS = dict(c=3, l_max=10, eps=0.3, tol=1e-3, drop="fixed")
 METRIC = "RSAI M-columns/sec at matched ||AM-I||_F, FP32+refine vs FP64; bwd/fwd ratio"
 WORKLOAD = "convdiff3d_7pt_upwind_64^3_Pe5"
-# norm1, tau, 4 bins (W, W2, C, G), 2 column-stats kernels, 2 x 3 scan kernels, pool->CSC, CSC->rows, row sort
-KERNELS_PER_BUILD = 17
+# norm1, tau, 4 bins (W, W2, C, G), 3 kernels ordering the global bin's queue, 2 column-stats kernels,
+# 2 x 3 scan kernels, pool->CSC, CSC->rows, row sort
+KERNELS_PER_BUILD = 20
 # nominal CUDA-core rates (152 SMs): FP32 = 152 x 128 lanes x 2 flop x 2.07 GHz; FP64 as published for GB300
 PEAK_FP32_NOMINAL = 152 * 128 * 2 * 2.07e9
 PEAK_FP64_NOMINAL = 1.25e12

@@ -17,6 +17,13 @@ __global__ void k_csc_from_csr(const double *csr_val, const int64_t *csc_to_csr,
 __global__ void k_norm1(const int64_t *col_ptr, const double *cval, int64_t n, const int32_t *col_block,
                         double *out);
 __global__ void k_collect_failed(const int32_t *flags, int64_t n, int32_t *list, uint32_t *count);
+// largest-first order of a column queue (cost buckets: bit length of a proxy)
+constexpr int kCostBuckets = 32;
+__global__ void k_cost_buckets(const int32_t *list, const uint32_t *count, const int64_t *col_ptr,
+                               const int32_t *row_idx, const int64_t *row_ptr, uint8_t *bucket, uint32_t *hist);
+__global__ void k_cost_offsets(uint32_t *hist);
+__global__ void k_cost_scatter(const int32_t *list, const uint32_t *count, const uint8_t *bucket, uint32_t *offset,
+                               int32_t *out);
 __global__ void k_col_block(const int64_t *cstart, int32_t nblocks, int64_t n, int32_t *col_block);
 __global__ void k_shift_ptr(int64_t *ptr, int64_t n, const int32_t *col_block, const int64_t *estart,
                             int64_t nnz_total);

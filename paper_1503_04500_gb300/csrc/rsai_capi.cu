@@ -54,6 +54,9 @@ struct rsai_handle {
     // W2->C, C->G; [7] columns of a pool-overflow rerun
     uint32_t *qnext = nullptr;
     int32_t *ovf1 = nullptr, *ovf2 = nullptr, *ovf3 = nullptr;
+    int32_t *ovf3_sorted = nullptr;  // the global bin's queue, largest column first
+    uint8_t *cost_bucket = nullptr;
+    uint32_t *cost_hist = nullptr;   // [kCostBuckets]
     int64_t ovf_cap = 0;
     // per column
     int64_t *col_off = nullptr;
@@ -228,7 +231,7 @@ cudaError_t enqueue_bins(rsai_handle *h, int mode, const DevA &A, const Frozen &
     ColQueue QW{wlist, wcount, n, h->qnext + 0, h->ovf1, h->qnext + 4, h->ovf_cap};
     ColQueue QW2{h->ovf1, h->qnext + 4, n, h->qnext + 1, h->ovf2, h->qnext + 5, h->ovf_cap};
     ColQueue QC{h->ovf2, h->qnext + 5, n, h->qnext + 2, h->ovf3, h->qnext + 6, h->ovf_cap};
-    ColQueue QG{h->ovf3, h->qnext + 6, n, h->qnext + 3, nullptr, nullptr, 0};
+    ColQueue QG{h->ovf3_sorted, h->qnext + 6, n, h->qnext + 3, nullptr, nullptr, 0};
     if (ev) cudaEventRecord(ev[1], st);
     cudaError_t e = launch_bin_warp(mode, fp32, h->grid_w, h->tuning.warp_bin_warps, A, P, h->capW, QW, O, F, gctr,
                                     false, st);
@@ -239,6 +242,14 @@ cudaError_t enqueue_bins(rsai_handle *h, int mode, const DevA &A, const Frozen &
     e = launch_bin_block(mode, fp32, h->grid_c, A, P, h->capC, QC, O, F, gctr, false, nullptr, 0, 1, st);
     if (e != cudaSuccess) return e;
     if (before_global && before_global(h, st) != RSAI_OK) return cudaErrorMemoryAllocation;
+    // the columns that reached the global bin, largest first (grids cover n;
+    // the device-side count bounds the work)
+    cudaMemsetAsync(h->cost_hist, 0, sizeof(uint32_t) * kCostBuckets, st);
+    k_cost_buckets<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(h->ovf3, h->qnext + 6, A.col_ptr, A.row_idx,
+                                                                 A.row_ptr, h->cost_bucket, h->cost_hist);
+    k_cost_offsets<<<1, 32, 0, st>>>(h->cost_hist);
+    k_cost_scatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(h->ovf3, h->qnext + 6, h->cost_bucket, h->cost_hist,
+                                                                 h->ovf3_sorted);
     if (ev) cudaEventRecord(ev[3], st);
     e = launch_bin_block(mode, fp32, h->grid_g, A, P, h->capG, QG, O, F, gctr, true, h->gwork, h->gstride, 2, st);
     return e;
@@ -475,6 +486,9 @@ int build_common(rsai_handle *h, cudaStream_t st) {
     TRY(dalloc(h, &h->ovf1, n, st));
     TRY(dalloc(h, &h->ovf2, n, st));
     TRY(dalloc(h, &h->ovf3, n, st));
+    TRY(dalloc(h, &h->ovf3_sorted, n, st));
+    TRY(dalloc(h, &h->cost_bucket, n, st));
+    TRY(dalloc(h, &h->cost_hist, kCostBuckets, st));
     TRY(dalloc(h, &h->col_off, n, st));
     TRY(dalloc(h, &h->col_len, n, st));
     TRY(dalloc(h, &h->col_q, n, st));

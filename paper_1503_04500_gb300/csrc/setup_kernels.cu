@@ -333,6 +333,49 @@ __global__ void k_sort_rows(const int64_t *Mrowptr, const int32_t *tcols, const 
     }
 }
 
+// ---------------------------------------------------------------------------
+// largest-first order of the global bin's queue (longest processing time
+// first, so that the biggest columns do not start last and leave the other
+// SMs idle).  Cost proxy of column k: the entries of the rows of A(:,k), i.e.
+// the size of the first candidate set of new columns (Algorithm 1 step 5);
+// columns are bucketed by its bit length, buckets taken in decreasing order.
+
+__global__ void k_cost_buckets(const int32_t *list, const uint32_t *count, const int64_t *col_ptr,
+                               const int32_t *row_idx, const int64_t *row_ptr, uint8_t *bucket,
+                               uint32_t *hist /* [kCostBuckets] */) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)*count) return;
+    const int32_t k = list[t];
+    int64_t cost = 0;
+    for (int64_t e = col_ptr[k]; e < col_ptr[k + 1]; ++e) {
+        const int32_t i = row_idx[e];
+        cost += row_ptr[i + 1] - row_ptr[i];
+    }
+    const int b = min(kCostBuckets - 1, 64 - __clzll((unsigned long long)cost));
+    bucket[t] = (uint8_t)b;
+    atomicAdd(&hist[b], 1u);
+}
+
+// hist -> start offsets, largest bucket first (one warp)
+__global__ void k_cost_offsets(uint32_t *hist) {
+    const int lane = threadIdx.x;
+    uint32_t v = (lane < kCostBuckets) ? hist[kCostBuckets - 1 - lane] : 0u;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane < kCostBuckets) hist[kCostBuckets - 1 - lane] = incl - v;
+}
+
+__global__ void k_cost_scatter(const int32_t *list, const uint32_t *count, const uint8_t *bucket, uint32_t *offset,
+                               int32_t *out) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)*count) return;
+    out[atomicAdd(&offset[bucket[t]], 1u)] = list[t];
+}
+
 // adjoint launcher
 cudaError_t launch_adjoint_gather(int64_t n, int64_t nnzM, const int64_t *row_ptr, const int32_t *col_idx,
                                   const int64_t *Mrowptr, const int32_t *Mcols, const int64_t *Mcsc_to_csr,
