@@ -50,6 +50,28 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def rank_barrier(pg) -> None:
+    """Barrier over the replicas (no-op for one process)."""
+    if pg is not None:
+        pg.barrier()
+
+
+def rank_max(pg, x: float, device: str) -> float:
+    """The maximum of x over the replicas: the whole job's time is the slowest rank's."""
+    if pg is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas, each doing `units_per_rank` in the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 class ClockSampler:
     """nvidia-smi samples (200 ms) while running; summary of the samples under load."""
 
@@ -213,16 +235,11 @@ def main():
         pg = dist
 
     def barrier():
-        if pg is not None:
-            pg.barrier()
+        rank_barrier(pg)
         torch.cuda.synchronize()
 
     def max_over_ranks(x: float) -> float:
-        if pg is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(pg, x, "cuda")
 
     rsai.load()
     A = inputs.convdiff3d(64)
@@ -368,7 +385,7 @@ def main():
                 e2e_t.append(t1 - t0)
             d2h = 8 * (A.n + 1) + 12 * st["nnz_M"] + 200
         e2e_s = max_over_ranks(sum(e2e_t) / len(e2e_t))
-        e2e = {"value": world * A.n / e2e_s, "unit": "columns/s", "h2d_bytes_per_step": h2d,
+        e2e = {"value": job_throughput(world, A.n, e2e_s), "unit": "columns/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s}
 
     # parametric 2-D problem (256^2, A(theta) = L/h^2 + theta1 Cx + theta2 Cy): forward and adjoint
@@ -429,7 +446,7 @@ def main():
                "sample": f"all {ncols} columns of the workload, FP64, {threads} threads", "seconds": dt,
                "frob_oracle": Mo.frob()}
 
-    value = world * A.n / (dev_ms / 1e3)
+    value = job_throughput(world, A.n, dev_ms / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": "columns/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms, "higher_is_better": True, "scaling": "weak",
@@ -437,7 +454,7 @@ def main():
         "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, **PARAMS, "precision": "fp32_refine",
                    "l2": "flushed (256 MB write) between timed steps", "replicas": world},
         "frob": s32["frob"], "nnz_M": s32["nnz_M"], "n_c": s32["n_c"],
-        "fp64": {"value": world * A.n / (dev_ms64 / 1e3), "ms_per_step": dev_ms64, "frob": s64["frob"],
+        "fp64": {"value": job_throughput(world, A.n, dev_ms64 / 1e3), "ms_per_step": dev_ms64, "frob": s64["frob"],
                  "nnz_M": s64["nnz_M"], "roofline": roof64, "phases_ms": ph64},
         "frob_rel_diff_fp32r_vs_fp64": abs(s32["frob"] - s64["frob"]) / s64["frob"],
         "speedup_fp32r_vs_fp64": dev_ms64 / dev_ms,
