@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -77,7 +78,8 @@ class ClockSampler:
 
     def __init__(self, uuid: str | None):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the raw samples go to a temporary file; the line printed carries their summary
+        self.path = os.path.join(os.environ.get("RSAI_CLOCKS_DIR", tempfile.gettempdir()), f"rsai_clocks_{os.getpid()}.csv")
         self.uuid = uuid
 
     def __enter__(self):
