@@ -5,6 +5,7 @@ built on Aᵀ by the same kernels).
 
     python -m paper_1503_04500_gb300.sweep --workload convdiff3d --size 32 \
         --eps 0.2,0.3,0.4 --c 3,5 --lmax 5,10 --precision fp32_refine
+    python -m paper_1503_04500_gb300.sweep --batch 64 --size 5000 --precision fp32_refine
 
 One JSON line per setting: spar = nnz(M)/nnz(A), ||AM - I||_F (or ||MA - I||_F),
 n_c (columns with ||r_k|| > ε), the build time (median of graph-replayed
@@ -84,6 +85,60 @@ def run(workload="convdiff2d", size=20, seed=1503, eps=(0.3,), c=(3,), lmax=(10,
         yield out
 
 
+def run_batch(count=64, nmax=5000, precision="fp32_refine", c=3, l_max=10, eps=0.3, drop="fixed", tol=1e-3,
+              rebuilds=5):
+    """The batch configuration at a chosen size: `count` members (half
+    convection-diffusion, half power law, n uniform in [1000, nmax]) built as one
+    block-diagonal problem in one graph.  Returns the aggregate columns/s of the
+    graph-replayed build, the backward time on the frozen pattern, and, for an
+    FP32+refine batch, the largest relative ||A_b M_b - I||_F difference per
+    member from the FP64 build of the same batch."""
+    import numpy as np
+    import torch
+
+    members = [inputs.random_batch_member(i, nmax=nmax) for i in range(count)]
+    ntot = sum(A.n for A in members)
+    kw = dict(c=c, l_max=l_max, eps=eps, drop=drop, tol=tol)
+    h = rsai.build_batch(members, precision=precision, **kw)
+    st = torch.cuda.current_stream()
+    times = []
+    for _ in range(rebuilds):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        h.rebuild()
+        e1.record(st)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    fwd_ms = statistics.median(times)
+    frob, nc, nz = h.block_stats(count)
+    # backward on the frozen pattern (the members' values side by side)
+    vals = torch.as_tensor(np.concatenate([A.val for A in members]), device="cuda")
+    nnzM = h.stats()["nnz_M"]
+    gM = torch.ones(nnzM, dtype=torch.float64, device="cuda")
+    h.backward(vals, gM)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    h.backward(vals, gM)
+    e1.record(st)
+    torch.cuda.synchronize()
+    bwd_ms = e0.elapsed_time(e1)
+    s = h.stats()
+    h.free()
+    rel = None
+    if precision != "fp64":
+        h64 = rsai.build_batch(members, precision="fp64", **kw)
+        frob64, _, _ = h64.block_stats(count)
+        h64.free()
+        rel = float(np.max(np.abs(frob - frob64) / frob64))
+    return {"workload": f"batch of {count} (n in [1000, {nmax}])", "members": count, "n_total": ntot,
+            "nnz_A": int(sum(A.nnz for A in members)), "precision": precision, "cols_bin": s["cols_bin"],
+            "build_ms": fwd_ms, "columns_per_s": ntot / (fwd_ms / 1e3), "bwd_ms": bwd_ms,
+            "bwd_fwd_ratio": bwd_ms / fwd_ms, "max_member_frob_rel_diff_vs_fp64": rel}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--workload", default="convdiff2d",
@@ -101,7 +156,13 @@ def main(argv=None):
     ap.add_argument("--no-solve", dest="solve", action="store_false")
     ap.add_argument("--init", default="identity", choices=["identity", "A"],
                     help="initial pattern J_k^(0): {k} or the rows of column k of A")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="instead of a sweep: a batch of this many random members (n up to --size) in one build")
     a = ap.parse_args(argv)
+    if a.batch > 0:
+        print(json.dumps(run_batch(a.batch, a.size, a.precision, _ints(a.c)[0], _ints(a.lmax)[0], _floats(a.eps)[0],
+                                   a.drop, a.tol, max(a.rebuilds, 1))), flush=True)
+        return
     for row in run(a.workload, a.size, a.seed, _floats(a.eps), _ints(a.c), _ints(a.lmax), a.drop, a.tol,
                    a.precision, a.side, a.rebuilds, a.solve, a.init):
         print(json.dumps(row), flush=True)
