@@ -263,6 +263,21 @@ def random_batch_member(i: int, seed0: int = 1503, nmin: int = 1000, nmax: int =
     return powerlaw(n, seed=seed0 + i)
 
 
+def matrix_stats(A: SparseMatrix) -> dict:
+    """The statistics the paper's matrix table reports (Section 5): n, nnz,
+    p = nnz/n (average nonzeros per column), s = the number of irregular
+    columns (at least 10p nonzeros, the definition of Section 1), p_d = the
+    nonzeros of the densest column; and the same two counts for rows, whose
+    density is what makes RSAI's LS problems large (Section 4)."""
+    n = int(A.n)
+    nnz = int(A.nnz)
+    p = nnz / n if n else 0.0
+    col = np.diff(A.col_ptr)
+    row = np.diff(A.row_ptr)
+    return {"n": n, "nnz": nnz, "p": p, "s": int(np.sum(col >= 10 * p)), "p_d": int(col.max()) if n else 0,
+            "s_rows": int(np.sum(row >= 10 * p)), "p_d_rows": int(row.max()) if n else 0}
+
+
 def ones_rhs(A: SparseMatrix) -> np.ndarray:
     """b = A * (1,...,1)^T, the right-hand side of the paper's solver runs."""
     rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))

@@ -83,3 +83,17 @@ def test_transpose_swaps_formats_without_arithmetic():
     TT = rsai.transpose(T)
     for f in ("row_ptr", "col_idx", "val", "col_ptr", "row_idx", "cval", "csc_to_csr"):
         np.testing.assert_array_equal(getattr(TT, f), getattr(A, f))
+
+
+def test_matrix_stats_counts_irregular_columns_and_rows():
+    # 40 x 40: identity plus one dense column (all 40 rows) and one dense row (all 40 columns)
+    n = 40
+    rows = list(range(n)) + list(range(n)) + [7] * n
+    cols = list(range(n)) + [3] * n + list(range(n))
+    A = gen.from_coo(n, np.array(rows), np.array(cols), np.ones(len(rows)))
+    st = gen.matrix_stats(A)
+    nnz = n + (n - 1) + (n - 2)  # duplicates at (3,3), (7,7) and (7,3) are summed
+    assert st["nnz"] == nnz and st["p"] == pytest.approx(nnz / n)
+    assert st["s"] == 1 and st["p_d"] == n  # column 3 holds every row; 10p = 29.25 <= 40
+    assert st["s_rows"] == 1 and st["p_d_rows"] == n
+    assert gen.matrix_stats(gen.convdiff2d(8, (1.0, 1.0)))["s"] == 0  # a stencil is regular
