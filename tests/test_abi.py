@@ -92,3 +92,37 @@ def test_set_allocator_arguments(lib):
     assert lib.rsai_set_allocator(alloc, free, None) == 0
     assert lib.rsai_set_allocator(rsai.ALLOC_FN(), rsai.FREE_FN(), None) == 0
     assert seen == []  # nothing allocated by installing
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of rsai_csr, rsai_csc, rsai_params, rsai_stats and
+    rsai_tuning have the header's sizes and field offsets (gcc compiles the C
+    header and prints them)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"rsai_csr": rsai.CSR, "rsai_csc": rsai.CSC, "rsai_params": rsai.Params, "rsai_stats": rsai.Stats,
+               "rsai_tuning": rsai.Tuning}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rsai.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            name, field, value = line.split()
+            got[(name, field)] = int(value)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
