@@ -138,17 +138,20 @@ enum { RSAI_COL_CONVERGED = 1, RSAI_COL_RANK = 2, RSAI_COL_NONFINITE = 4, RSAI_C
 
 typedef struct rsai_handle rsai_handle;
 
-/* Library version (RSAI_ABI_VERSION). */
+/* Library version (RSAI_ABI_VERSION).  No counterpart in the paper. */
 int32_t rsai_abi_version(void);
 
-/* Text of a status code (static storage, never NULL). */
+/* Text of a status code (static storage, never NULL).  No counterpart in the
+ * paper. */
 const char *rsai_status_string(rsai_status s);
 
 /* Defaults of Section 3 / Section 5: c = 3, l_max = 10, eps = 0.3,
  * RSAI_DROP_FIXED with tol = 1e-3, RSAI_FP64, tie_band = 1e-12. */
 rsai_status rsai_params_default(rsai_params *p);
 
-/* Host-only validation of a parameter block (no device work). */
+/* Host-only validation of a parameter block (no device work): the ranges of
+ * Algorithm 1's c, l_max and eps (Section 3), the drop mode and tol of Eq. 4.3,
+ * and the flags.  Errors: INVALID_ARG. */
 rsai_status rsai_params_check(const rsai_params *p);
 
 /*
@@ -183,13 +186,14 @@ rsai_status rsai_build(const rsai_csr *A, const rsai_csc *Acsc, const rsai_param
 rsai_status rsai_build_batch(const rsai_csr *As, const rsai_csc *Acscs, int32_t count, const rsai_params *params,
                              void *stream, rsai_handle **out);
 
-/* Per-member ||A_b M_b - I||_F, n_c and nnz(M_b) of a batch handle (one entry
- * for a single-matrix handle); host arrays of `count` entries, any may be
- * NULL.  Synchronises the stream. */
+/* Per-member ||A_b M_b - I||_F (Eq. 2.1), n_c and nnz(M_b) (the Section 5
+ * metrics) of a batch handle (one entry for a single-matrix handle); host
+ * arrays of `count` entries, any may be NULL.  Synchronises the stream. */
 rsai_status rsai_get_block_stats(rsai_handle *h, void *stream, double *frob, int64_t *n_c, int64_t *nnz_M);
 
 /*
- * rsai_rebuild -- run the build again on the handle's own copy of A after
+ * rsai_rebuild -- Algorithm 1 with Eq. 4.3 over every column (Eq. 2.2) again,
+ * on the handle's own copy of A after
  * new values were written with rsai_set_values (same structure), reusing every
  * buffer: no allocation, no host synchronisation; the launch sequence is
  * recorded in a CUDA graph on first use and replayed afterwards.
@@ -197,21 +201,25 @@ rsai_status rsai_get_block_stats(rsai_handle *h, void *stream, double *frob, int
  */
 rsai_status rsai_rebuild(rsai_handle *h, void *stream);
 
-/* Overwrite the handle's copy of A's values (CSR order; host or device). */
+/* Overwrite the handle's copy of A's values (CSR order; host or device): the
+ * matrix whose LS problems (Eq. 2.3) the next rsai_rebuild solves, on the same
+ * structure.  The CSC copy follows on the device. */
 rsai_status rsai_set_values(rsai_handle *h, const double *A_val, void *stream);
 
-/* Statistics of the last build (synchronises the stream). */
+/* Statistics of the last build (synchronises the stream): ||AM - I||_F
+ * (Eq. 2.1), spar and n_c (Section 5) and the algorithmic work counters. */
 rsai_status rsai_get_stats(rsai_handle *h, void *stream, rsai_stats *out);
 
 /*
- * rsai_get_M -- copy M out in CSR: row_ptr[n+1] (int64), col_idx[nnz_M]
- * (int32), val[nnz_M]; any pointer may be NULL to skip it.  Sized by
- * rsai_stats.nnz_M.  Host or device destinations.
+ * rsai_get_M -- copy M (the columns m_k of Eq. 2.2) out in CSR: row_ptr[n+1]
+ * (int64), col_idx[nnz_M] (int32), val[nnz_M]; any pointer may be NULL to
+ * skip it.  Sized by rsai_stats.nnz_M.  Host or device destinations.
  */
 rsai_status rsai_get_M(rsai_handle *h, int64_t *row_ptr, int32_t *col_idx, double *val, void *stream);
 
-/* Per-column results: rho[k] = ||r_k||, loops[k], flags[k] (RSAI_COL_*);
- * NULL pointers are skipped.  Host or device destinations. */
+/* Per-column results: rho[k] = ||r_k|| (Eq. 2.4), loops[k] (l of Algorithm
+ * 1), flags[k] (RSAI_COL_*); NULL pointers are skipped.  Host or device
+ * destinations. */
 rsai_status rsai_get_columns(rsai_handle *h, double *rho, int32_t *loops, int32_t *flags, void *stream);
 
 /*
@@ -266,7 +274,8 @@ enum {
 };
 
 /*
- * rsai_build_phase_times -- run the build sequence of rsai_rebuild once more,
+ * rsai_build_phase_times -- no counterpart in the paper (timing of the build's
+ * phases for the roofline).  Runs the build sequence of rsai_rebuild once more,
  * launched phase by phase (not as a graph) with a CUDA event between phases on
  * `stream`, and write each phase's duration in milliseconds to
  * ms[RSAI_PHASE_COUNT].  Synchronises the stream.  The result of the build is
@@ -310,17 +319,19 @@ typedef struct {
     int32_t global_bin_ctas;      /* CTAs of the global bin, 0 = one per column that reaches it, <= SMs */
 } rsai_tuning;
 
-/* Read / replace a handle's launch shapes; the next rsai_rebuild records a new
- * graph.  Synchronises the handle's stream.  Errors: INVALID_ARG (a value out
+/* Read / replace a handle's launch shapes (no counterpart in the paper); the
+ * next rsai_rebuild records a new graph.  Synchronises the handle's stream.  Errors: INVALID_ARG (a value out
  * of range or a shape that cannot be resident), OOM. */
 rsai_status rsai_get_tuning(const rsai_handle *h, rsai_tuning *t);
 rsai_status rsai_set_tuning(rsai_handle *h, const rsai_tuning *t);
 
-/* Release a handle and its device memory (NULL is a no-op). */
+/* Release a handle and its device memory (NULL is a no-op).  No counterpart in
+ * the paper. */
 void rsai_handle_free(rsai_handle *h);
 
 /*
- * rsai_get_M_csc -- M's pattern in CSC, as the build assembled it:
+ * rsai_get_M_csc -- M's pattern in CSC (the patterns J_k of the columns m_k,
+ * Eq. 2.2), as the build assembled it:
  * col_ptr[n+1] (int64), row_idx[nnz_M] (int32, ascending within a column)
  * and csc_to_csr[nnz_M] (int64): the position in rsai_get_M's CSR value array
  * of each CSC entry, so that the CSC values of M (or of any array in M's CSR
@@ -378,7 +389,8 @@ typedef void (*rsai_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 rsai_status rsai_set_allocator(rsai_alloc_fn alloc, rsai_free_fn release, void *ctx);
 
 /*
- * rsai_peak_fma -- measure the CUDA-core FMA pipe rate: launches a grid of
+ * rsai_peak_fma -- no counterpart in the paper.  Measures the CUDA-core FMA
+ * pipe rate: launches a grid of
  * independent FMA chains (FP32 if fp64 == 0, FP64 otherwise) and returns the
  * achieved flop/s in *flops_per_s (2 flops per FMA).  Used for the roofline
  * of the build kernels.
