@@ -126,3 +126,16 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_product_path_never_reaches_the_oracle():
+    """Only tests, the smoke check and the benchmark's CPU legs may use the
+    oracle: no module of the package imports it, and the CUDA sources share no
+    file with it."""
+    pkg = os.path.join(ROOT, "paper_1503_04500_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import oracle|from oracle)", text, re.M), f
+                assert "rsai_oracle" not in text, f
