@@ -33,8 +33,10 @@ def _solve_normal(B, e):
     return [h[a] / G[a][a] for a in range(p)]
 
 
-def exact_rsai(A, c=3, l_max=10, eps=Fraction(3, 10), drop="fixed", tol=Fraction(1, 1000)):
+def exact_rsai(A, c=3, l_max=10, eps=Fraction(3, 10), drop="fixed", tol=Fraction(1, 1000), init="identity"):
     """Columns of M for a dense integer (or Fraction) matrix A (list of rows).
+    ``init``: the initial pattern J_k^(0) (Algorithm 1 step 1), "identity" ({k})
+    or "A" (the rows i with A[i][k] != 0).
 
     Returns a list of (J, m, rho2, loops) with J ascending, m exact Fractions,
     rho2 = ||r_k||^2 exact.
@@ -72,7 +74,7 @@ def exact_rsai(A, c=3, l_max=10, eps=Fraction(3, 10), drop="fixed", tol=Fraction
             r = {i: sum(A[i][j] * m[t] for t, j in enumerate(J)) - (1 if i == k else 0) for i in S}
             return r
 
-        J = [k]
+        J = [k] if init == "identity" else [i for i in range(n) if A[i][k] != 0]
         R = set()
         loops = 0
         m = solve(J)

@@ -265,3 +265,23 @@ def test_initial_pattern_of_A_is_the_least_squares_solution_on_it(c1):
     for t, k in enumerate(M2.cols):
         J, _ = M2.column(t)
         assert set(A.row_idx[A.col_ptr[k]:A.col_ptr[k + 1]]) <= set(J)
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("drop", ["none", "adaptive", "fixed"])
+def test_p9_exact_brute_force_initial_pattern_of_A(seed, drop):
+    """The oracle's initial pattern of A against exact rational RSAI started the same way."""
+    rng = np.random.default_rng(2000 + seed)
+    n = int(rng.integers(4, 9))
+    D = _small_int_matrix(rng, n)
+    c = int(rng.integers(1, 4))
+    lm = int(rng.integers(0, 4))
+    eps, tol = Fraction(1, 20), Fraction(3, 100)
+    ex = exact_rsai(D.tolist(), c=c, l_max=lm, eps=eps, drop=drop, tol=tol, init="A")
+    M = oracle.build(gen.from_dense(D), c=c, l_max=lm, eps=float(eps), drop=drop, tol=float(tol), init="A")
+    for t, (J, m, rho2, loops) in enumerate(ex):
+        Jo, vo = M.column(t)
+        assert list(Jo) == J, (t, Jo, J)
+        np.testing.assert_allclose(vo, [float(v) for v in m], rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(M.rho[t] ** 2, float(rho2), rtol=1e-10, atol=1e-15)
+        assert M.loops[t] == loops
