@@ -447,6 +447,10 @@ def main():
         cpu = {"value": ncols / dt, "unit": "columns/s", "cores": threads, "kind": "oracle",
                "sample": f"all {ncols} columns of the workload, FP64, {threads} threads", "seconds": dt,
                "frob_oracle": Mo.frob()}
+        # the same oracle on one thread, on every 16th column (columns are independent)
+        n1, dt1, _ = run_oracle_sample(A, 1, 16)
+        cpu["single_thread"] = {"value": n1 / dt1, "unit": "columns/s", "cores": 1,
+                                "sample": f"every 16th column ({n1} of {A.n}), FP64, 1 thread", "seconds": dt1}
 
     value = job_throughput(world, A.n, dev_ms / 1e3)
     line = {
