@@ -439,12 +439,14 @@ int size_global_slab(rsai_handle *h, cudaStream_t st) {
     int want = std::max(1, std::min(h->sms, (int)cnt));
     if (h->tuning.global_bin_ctas > 0) want = std::min(h->tuning.global_bin_ctas, h->sms);
     if (want <= h->grid_g) return RSAI_OK;
-    if (h->gwork) {
-        dfree(h, h->gwork, st);
-        h->gwork = nullptr;
-    }
+    // the larger slab first, so that a failed allocation leaves the old one in place
+    char *slab = nullptr;
+    const int rc = dalloc(h, &slab, h->gstride * (size_t)want, st);
+    if (rc != RSAI_OK) return rc;
+    if (h->gwork) dfree(h, h->gwork, st);
+    h->gwork = slab;
     h->grid_g = want;
-    return dalloc(h, &h->gwork, h->gstride * (size_t)h->grid_g, st);
+    return RSAI_OK;
 }
 
 // Everything after A (CSR, CSC, csc_to_csr space) and the block arrays are in
@@ -527,7 +529,9 @@ int build_common(rsai_handle *h, cudaStream_t st) {
         TRY(alloc_m(cap));
         TRY(cuda_status(enqueue_build(h, st, nullptr, size_global_slab)));
         int32_t *retry = nullptr;
-        for (int attempt = 0; attempt < 6; ++attempt) {
+        constexpr int kMaxRegrow = 6;
+        bool settled = false;
+        for (int attempt = 0; attempt <= kMaxRegrow; ++attempt) {
             unsigned long long top = 0;
             int32_t herr = 0;
             cudaMemcpyAsync(&top, h->pool_top, sizeof(top), cudaMemcpyDeviceToHost, st);
@@ -535,8 +539,10 @@ int build_common(rsai_handle *h, cudaStream_t st) {
             TRY(cuda_status(cudaStreamSynchronize(st)));
             if ((int64_t)top <= h->pool_cap) {
                 if (herr != 0) status = herr;
+                settled = true;
                 break;
             }
+            if (attempt == kMaxRegrow) break;  // the last rerun still found the pool full
             // grow the pool (copying what fits), M's buffers with it
             const int64_t old_cap = h->pool_cap;
             // new reservations start at `top`; the columns to redo need at most `top`
@@ -566,6 +572,8 @@ int build_common(rsai_handle *h, cudaStream_t st) {
                                          size_global_slab, retry, h->qnext + 7)));
             TRY(cuda_status(enqueue_build_tail(h, st, nullptr)));
         }
+        // columns still without room in the pool are flagged and counted as failed
+        if (!settled) status = RSAI_ERR_WORKSPACE;
     }
 #undef TRY
     return status;
@@ -1060,12 +1068,12 @@ rsai_status rsai_set_tuning(rsai_handle *h, const rsai_tuning *t) {
     if (t->global_bin_ctas > 0) {
         const int want = std::min(t->global_bin_ctas, h->sms);
         if (want > h->grid_g) {
-            if (h->gwork) {
-                dfree(h, h->gwork, st);
-                h->gwork = nullptr;
-            }
-            int rc = dalloc(h, &h->gwork, h->gstride * (size_t)want, st);
+            // the larger slab first, so that a failed allocation leaves the old one in place
+            char *slab = nullptr;
+            int rc = dalloc(h, &slab, h->gstride * (size_t)want, st);
             if (rc != RSAI_OK) return (rsai_status)rc;
+            if (h->gwork) dfree(h, h->gwork, st);
+            h->gwork = slab;
         }
         h->grid_g = want;
     }
