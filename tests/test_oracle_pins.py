@@ -285,3 +285,29 @@ def test_p9_exact_brute_force_initial_pattern_of_A(seed, drop):
         np.testing.assert_allclose(vo, [float(v) for v in m], rtol=1e-12, atol=1e-15)
         np.testing.assert_allclose(M.rho[t] ** 2, float(rho2), rtol=1e-10, atol=1e-15)
         assert M.loops[t] == loops
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("drop", ["none", "adaptive", "fixed"])
+def test_p9_exact_brute_force_zero_diagonal(seed, drop):
+    """Structurally zero diagonal entries (a row permutation of a diagonally
+    dominant matrix): r_k lives on S = I u {k} with r(k) = -1 while k is not
+    in I, and m_kk = 0 on J = {k}.  Oracle against exact rational RSAI."""
+    rng = np.random.default_rng(3000 + seed)
+    n = int(rng.integers(4, 9))
+    while True:
+        D = _small_int_matrix(rng, n)[rng.permutation(n)]
+        if np.any(np.diag(D) == 0):
+            break
+    assert abs(np.linalg.det(D)) > 0.5  # integer matrix, nonsingular
+    c = int(rng.integers(1, 4))
+    lm = int(rng.integers(1, 5))
+    eps, tol = Fraction(1, 20), Fraction(3, 100)
+    ex = exact_rsai(D.tolist(), c=c, l_max=lm, eps=eps, drop=drop, tol=tol)
+    M = oracle.build(gen.from_dense(D), c=c, l_max=lm, eps=float(eps), drop=drop, tol=float(tol))
+    for t, (J, m, rho2, loops) in enumerate(ex):
+        Jo, vo = M.column(t)
+        assert list(Jo) == J, (t, Jo, J)
+        np.testing.assert_allclose(vo, [float(v) for v in m], rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(M.rho[t] ** 2, float(rho2), rtol=1e-10, atol=1e-15)
+        assert M.loops[t] == loops
