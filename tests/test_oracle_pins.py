@@ -311,3 +311,15 @@ def test_p9_exact_brute_force_zero_diagonal(seed, drop):
         np.testing.assert_allclose(vo, [float(v) for v in m], rtol=1e-12, atol=1e-15)
         np.testing.assert_allclose(M.rho[t] ** 2, float(rho2), rtol=1e-10, atol=1e-15)
         assert M.loops[t] == loops
+
+
+@pytest.mark.parametrize("delta,band,row", [(1e-13, 1e-12, 1), (1e-13, 0.0, 2), (1e-6, 1e-12, 2), (0.0, 0.0, 1)])
+def test_tie_band_reading(delta, band, row):
+    """Reading of step 4's order: residual entries within tie_band * ||r||_inf of
+    the c-th largest count as tied and are taken by lowest index.  Column 0 of
+    [[4,0,0],[1,4,0],[1+delta,0,4]] has r = (4m-1, m, (1+delta)m) at loop 0, so
+    with c = 1 row 2 is strictly largest; rows 1 and 2 bring columns 1 and 2."""
+    D = np.array([[4.0, 0.0, 0.0], [1.0, 4.0, 0.0], [1.0 + delta, 0.0, 4.0]])
+    M = oracle.build(gen.from_dense(D), c=1, l_max=1, eps=1e-12, drop="none", tie_band=band)
+    J, _ = M.column(0)
+    assert list(J) == [0, row]
