@@ -137,14 +137,40 @@ class ClockSampler:
 BIN_KERNEL_SOURCES = ("build_kernels.cu", "column.cuh", "common.cuh", "warp_small.cuh")
 
 
+def strip_comments(src: str) -> str:
+    """C++ source without its comments, trailing blanks and empty lines (string
+    and character literals kept): what the compiler sees, up to line breaks."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        if src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            end = n if j < 0 else j + 2
+            out.append("\n" * src.count("\n", i, end))
+            i = end
+        elif src[i] in "\"'":
+            j = i + 1
+            while j < n and src[j] != src[i]:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        else:
+            out.append(src[i])
+            i += 1
+    return "\n".join(ln.rstrip() for ln in "".join(out).split("\n") if ln.strip())
+
+
 def kernel_source_hash() -> str:
-    """Hash of the bin kernels' sources: a committed ncu traffic figure is used only while it matches."""
+    """Hash of the bin kernels' sources without their comments: a committed ncu
+    traffic figure is used only while the code it was taken on is unchanged."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1503_04500_gb300", "csrc")
     for name in BIN_KERNEL_SOURCES:
-        with open(os.path.join(csrc, name), "rb") as f:
+        with open(os.path.join(csrc, name), encoding="utf-8") as f:
             h.update(name.encode())
-            h.update(f.read())
+            h.update(strip_comments(f.read()).encode())
     return h.hexdigest()[:16]
 
 
