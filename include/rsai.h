@@ -6,9 +6,9 @@
  * at a time (Eq. 2.2): for each k it solves the small least-squares problem
  * min ||A(I_k,J_k) m - e_k(I_k)|| (Eq. 2.3) by Householder QR, forms the
  * residual r_k = A m_k - e_k (Eq. 2.4), picks the c largest |r_k(i)| not used
- * before (Algorithm 1 step 4, Eq. 3.2), adds the columns of those rows of A to
- * J_k (step 5), drops entries |m_jk| <= tol_k (Eq. 4.3) and loops until
- * ||r_k|| <= eps or l_max loops (step 3).
+ * before (Algorithm 1, Eq. 3.2), adds the columns of those rows of A to J_k
+ * (Algorithm 1), drops entries |m_jk| <= tol_k (Eq. 4.3) and loops until
+ * ||r_k|| <= eps or l_max loops (Algorithm 1).
  *
  * Conventions for every entry point:
  *   - Indices are 0-based, int32 for row/column indices, int64 for pointers
@@ -93,11 +93,11 @@ enum {
     RSAI_FLAG_CHECKED = 1u,       /* accepted, no effect: the input checks (ranges, sortedness, the
                                      CSR/CSC pairing) always run and report status codes */
     RSAI_FLAG_INIT_PATTERN_A = 2u /* initial pattern J_k^(0) = rows of column k of A instead of {k}
-                                     (Algorithm 1 step 1 leaves it to the user; Section 3 suggests
+                                     (Algorithm 1 leaves it to the user; Section 3 suggests
                                      that of I, the default, when A has a nonzero diagonal) */
 };
 
-/* Parameters of RSAI(tol) (Algorithm 1 step 1; Section 3 defaults c ~ 3,
+/* Parameters of RSAI(tol) (Algorithm 1; Section 3 defaults c ~ 3,
  * eps = 0.1..0.4, l_max ~ 10; Eq. 4.3). */
 typedef struct {
     int32_t c;          /* dominant rows per loop (|Rhat_k|), 1..32 */

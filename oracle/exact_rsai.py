@@ -35,7 +35,7 @@ def _solve_normal(B, e):
 
 def exact_rsai(A, c=3, l_max=10, eps=Fraction(3, 10), drop="fixed", tol=Fraction(1, 1000), init="identity"):
     """Columns of M for a dense integer (or Fraction) matrix A (list of rows).
-    ``init``: the initial pattern J_k^(0) (Algorithm 1 step 1), "identity" ({k})
+    ``init``: the initial pattern J_k^(0) (Algorithm 1), "identity" ({k})
     or "A" (the rows i with A[i][k] != 0).
 
     Returns a list of (J, m, rho2, loops) with J ascending, m exact Fractions,

@@ -7,22 +7,22 @@
  * CPU-baseline leg of the benchmark may load this file's library.  It shares no
  * code, header, table or helper with the CUDA path.  It is written to be read
  * against the paper, not to be fast: every LS problem is refactored from
- * scratch by a textbook Householder QR, sets are sorted arrays, and loops follow
- * Algorithm 1 step by step.
+ * scratch by a textbook Householder QR, sets are sorted arrays, and the loop
+ * follows Algorithm 1 in the paper's order.
  *
  * What it computes, per column k (Section 2 Eq. 2.2-2.4, Section 3 Algorithm 1,
  * Section 4 Eq. 4.3):
- *   J = J0(k), R = {}, l = 0                         (Algorithm 1 step 1)
+ *   J = J0(k), R = {}, l = 0                         (initial pattern)
  *     J0(k) = {k} (the pattern of I, the paper's usual choice) or the
  *     pattern of column k of A (init_mode 1)
- *   Solve(J); Drop(J); r = A m - e_k; rho = ||r||    (step 2 + Eq. 4.3)
- *   while rho > eps and l < l_max                    (step 3)
- *     L = {i in S : |r_i| > band};  Cand = L \ R     (step 4, Eq. 3.2)
+ *   Solve(J); Drop(J); r = A m - e_k; rho = ||r||    (first solve, Eq. 4.3)
+ *   while rho > eps and l < l_max                    (loop test)
+ *     L = {i in S : |r_i| > band};  Cand = L \ R     (dominant indices, Eq. 3.2)
  *     if Cand empty: stop (r = 0 to working precision)
  *     Rhat = top-c of Cand by (|r_i| desc, i asc) with tie band; R += Rhat
- *     Jhat = cols(A(Rhat,:)) \ J                     (step 5)
- *     l = l + 1; if Jhat empty: continue             (step 6)
- *     J += Jhat; Solve(J); Drop(J); r, rho           (step 7 + Eq. 4.3)
+ *     Jhat = cols(A(Rhat,:)) \ J                     (new columns)
+ *     l = l + 1; if Jhat empty: continue             (empty Jhat)
+ *     J += Jhat; Solve(J); Drop(J); r, rho           (update of m_k, Eq. 4.3)
  *
  * Readings of points the paper leaves open (each is restated in the design
  * notes of the repository):
@@ -41,8 +41,9 @@
  *   - Ties: with v the c-th largest |r_i| of Cand and b = tie_band*||r||_inf,
  *     take every i with |r_i| > v + b, then fill up to c from
  *     {i : v - b <= |r_i| <= v + b} by lowest index; "r_i != 0" means |r_i| > b.
- *   - Algorithm 1 step 4 always excludes R (not only on a repeat); loops whose
- *     Jhat is empty still count toward l_max (step 6).
+ *   - The choice of dominant indices always excludes R (not only on a
+ *     repeat); loops whose Jhat is empty still count toward l_max (Algorithm 1
+ *     raises l before it returns to its loop test).
  *   - Rank: if |R_jj| <= q*u*||B||_F the column is flagged RANK and that
  *     component of m is set to zero.
  *
@@ -301,7 +302,7 @@ static void rsai_column(const omat *A, const oparams *P, int64_t k, ocol *out, o
     double qr_flops = 0.0, res_flops = 0.0, bytes = 0.0, rho = 0.0, nnzJ = 0.0;
     J[0] = (int32_t)k;
     if (P->init_mode == 1) {
-        /* Algorithm 1 step 1 with the initial pattern of A: J = rows of A(:,k) */
+        /* Algorithm 1 started from the initial pattern of A: J = rows of A(:,k) */
         int64_t len = A->col_ptr[k + 1] - A->col_ptr[k];
         if (len > 0) {
             J = grow(J, &capJ, len, sizeof(int32_t));
@@ -353,7 +354,7 @@ static void rsai_column(const omat *A, const oparams *P, int64_t k, ocol *out, o
     res_flops += 2.0 * nnzJ + 2.0 * (double)s;
 
     while (rho > P->eps && l < P->l_max) {
-        /* step 4: dominant rows among L \ R */
+        /* dominant rows among L \ R (Algorithm 1, Eq. 3.2) */
         double rinf = 0.0;
         for (int64_t i = 0; i < s; ++i) if (fabs(w->r[i]) > rinf) rinf = fabs(w->r[i]);
         double band = P->tie_band * rinf;
@@ -391,7 +392,7 @@ static void rsai_column(const omat *A, const oparams *P, int64_t k, ocol *out, o
             bytes += 4.0 * (double)(A->row_ptr[Rhat[t] + 1] - A->row_ptr[Rhat[t]]) + 16.0;
         }
         nR = (int)sort_unique(Rset, nR);
-        /* step 5: Jhat = cols(A(Rhat,:)) \ J */
+        /* new columns: Jhat = cols(A(Rhat,:)) \ J */
         int64_t tot = 0;
         for (int t = 0; t < nh; ++t) tot += A->row_ptr[Rhat[t] + 1] - A->row_ptr[Rhat[t]];
         w->tmp = grow(w->tmp, &w->capT, tot + 1, sizeof(int32_t));
@@ -402,10 +403,10 @@ static void rsai_column(const omat *A, const oparams *P, int64_t k, ocol *out, o
                 if (find(J, p, j) < 0) w->tmp[nj++] = j;
             }
         nj = sort_unique(w->tmp, nj);
-        /* step 6 */
+        /* l = l + 1; an empty Jhat goes back to the loop test */
         ++l;
         if (nj == 0) continue;
-        /* step 7: J = J u Jhat (sorted), update the LS solution, drop, residual */
+        /* J = J u Jhat (sorted), update the LS solution, drop, residual */
         J = grow(J, &capJ, p + nj, sizeof(int32_t));
         m = realloc(m, sizeof(double) * (size_t)capJ);
         for (int64_t t = 0; t < nj; ++t) { J[p + t] = w->tmp[t]; NOTE_COLUMN(w->tmp[t]); }

@@ -121,7 +121,7 @@ class OracleM:
 def build(A, c=3, l_max=10, eps=0.3, drop="fixed", tol=1e-3, tie_band=1e-12, cols=None, threads=0,
           init="identity") -> OracleM:
     """RSAI(tol) columns of M (Algorithm 1 + Eq. 4.3) for the given columns.
-    ``init``: the initial pattern J_k^(0) of Algorithm 1 step 1, "identity" ({k})
+    ``init``: the initial pattern J_k^(0) of Algorithm 1, "identity" ({k})
     or "A" (the rows of column k of A)."""
     lib = _load()
     args = _mat(A)

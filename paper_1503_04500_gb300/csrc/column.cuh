@@ -5,10 +5,10 @@
 //   solve(J); drop(J); r = A m - e_k on S = I u {k}; rho = ||r||
 //   while rho > eps and l < l_max:
 //     Rhat = top-c of {i in S : |r_i| > band, i not in R} by (|r_i| desc, i asc)
-//            with a tie band; R += Rhat                        (step 4, Eq. 3.2)
-//     Jhat = cols(A(Rhat,:)) \ J                               (step 5)
-//     l += 1; if Jhat is empty: continue                       (step 6)
-//     J += Jhat; solve(J); drop(J); residual                   (step 7, Eq. 4.3)
+//            with a tie band; R += Rhat                        (Eq. 3.2)
+//     Jhat = cols(A(Rhat,:)) \ J
+//     l += 1; if Jhat is empty: continue
+//     J += Jhat; solve(J); drop(J); residual                   (Eq. 4.3)
 //
 // solve(J): I = rows of A(:,J) (Section 2), B = A(I,J) gathered into the team's
 // workspace (column-major, leading dimension q), e = e_k(I), Householder QR of
@@ -997,7 +997,7 @@ template <class Team, typename T> struct Column {
         return true;
     }
 
-    // Top-c dominant rows of S \ R (Algorithm 1 step 4) into w.Rhat; returns
+    // Top-c dominant rows of S \ R (Algorithm 1, Eq. 3.2) into w.Rhat; returns
     // their number (0: no candidate left).  |r_i| enters only as ordered
     // integer keys; the tie band needs three double operations per call.
     __device__ int dominant_rows() {
@@ -1309,7 +1309,7 @@ template <class Team, typename T> struct Column {
         if (me == 0) w.J[0] = k;
         team.sync();
         if (P.init_a) {
-            // Algorithm 1 step 1 with the initial pattern of A, solved by the
+            // Algorithm 1 started from the initial pattern of A, solved by the
             // general path below
             long long b = 0;
             const int len = pattern_of_column(team, A.col_ptr, A.row_idx, k, cap.pcap, w.J, &b);
@@ -1350,7 +1350,7 @@ template <class Team, typename T> struct Column {
                 int nj = new_columns(nh);
                 if (nj < 0) return COL_OVERFLOW;
                 ++l;
-                if (nj == 0) continue;  // Algorithm 1 step 6: next dominant rows
+                if (nj == 0) continue;  // empty Jhat: back to the loop test (Algorithm 1)
                 note_bytes_columns(0, nj, w.buf);
                 if (!merge_J(nj)) return COL_OVERFLOW;
                 grown = true;

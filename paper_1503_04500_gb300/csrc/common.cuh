@@ -30,7 +30,7 @@ struct DevA {
 // Parameters as the kernels see them (rsai_params plus derived values).
 struct DevParams {
     int c, l_max, drop_mode, precision;
-    int init_a;  // initial pattern J_k^(0): 0 = {k}, 1 = rows of A(:,k) (Algorithm 1 step 1)
+    int init_a;  // initial pattern J_k^(0) of Algorithm 1: 0 = {k}, 1 = rows of A(:,k)
     double eps, tol, tie_band;
     const double *norm1;       // ||A||_1 per block (one block unless a batch)
     const double *tau_fixed;   // tol / ||A||_1 per block

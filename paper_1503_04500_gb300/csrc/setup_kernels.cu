@@ -337,7 +337,7 @@ __global__ void k_sort_rows(const int64_t *Mrowptr, const int32_t *tcols, const 
 // largest-first order of the global bin's queue (longest processing time
 // first, so that the biggest columns do not start last and leave the other
 // SMs idle).  Cost proxy of column k: the entries of the rows of A(:,k), i.e.
-// the size of the first candidate set of new columns (Algorithm 1 step 5);
+// the size of the first candidate set of new columns (Algorithm 1);
 // columns are bucketed by its bit length, buckets taken in decreasing order.
 
 __global__ void k_cost_buckets(const int32_t *list, const uint32_t *count, const int64_t *col_ptr,

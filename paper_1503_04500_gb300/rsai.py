@@ -213,7 +213,7 @@ def default_params(**kw) -> Params:
         elif k == "precision":
             p.precision = PRECISION[v] if isinstance(v, str) else int(v)
         elif k == "init":
-            # initial pattern J_k^(0) (Algorithm 1 step 1): "identity" ({k}) or "A" (rows of A(:,k))
+            # initial pattern J_k^(0) (Algorithm 1): "identity" ({k}) or "A" (rows of A(:,k))
             p.flags = (p.flags & ~FLAG_INIT_PATTERN_A) | (FLAG_INIT_PATTERN_A if v == "A" else 0)
         else:
             setattr(p, k, v)

@@ -399,7 +399,7 @@ def test_sweep_rows_and_monotone_residual():
 
 @pytest.mark.parametrize("drop", ["fixed", "none"])
 def test_initial_pattern_of_A(c1, drop):
-    """Algorithm 1 step 1 with J_k^(0) = rows of A(:,k) (RSAI_FLAG_INIT_PATTERN_A):
+    """Algorithm 1 started from J_k^(0) = rows of A(:,k) (RSAI_FLAG_INIT_PATTERN_A):
     FP64 patterns bit-identical to the oracle's, values to 1e-10, the same
     work counters; FP32+refine within the FP32 tolerances."""
     h, dA, res, rho, loops, flags, st = gpu_M(c1, drop=drop, precision="fp64", init="A", **PARAMS_C1)

@@ -244,7 +244,7 @@ def test_golden_exact_small():
 
 
 def test_initial_pattern_of_A_is_the_least_squares_solution_on_it(c1):
-    """Algorithm 1 step 1 with J_k^(0) = rows of column k of A and no loop
+    """Algorithm 1 started from J_k^(0) = rows of column k of A and no loop
     (l_max = 0, no dropping): every column is the LS minimiser of
     ||A(:,J) m - e_k|| on that pattern, which NumPy's lstsq gives directly."""
     A = gen.convdiff2d(10, (7.0, -3.0))
@@ -315,8 +315,9 @@ def test_p9_exact_brute_force_zero_diagonal(seed, drop):
 
 @pytest.mark.parametrize("delta,band,row", [(1e-13, 1e-12, 1), (1e-13, 0.0, 2), (1e-6, 1e-12, 2), (0.0, 0.0, 1)])
 def test_tie_band_reading(delta, band, row):
-    """Reading of step 4's order: residual entries within tie_band * ||r||_inf of
-    the c-th largest count as tied and are taken by lowest index.  Column 0 of
+    """Reading of the order of Algorithm 1's dominant indices: residual entries
+    within tie_band * ||r||_inf of the c-th largest count as tied and are taken
+    by lowest index.  Column 0 of
     [[4,0,0],[1,4,0],[1+delta,0,4]] has r = (4m-1, m, (1+delta)m) at loop 0, so
     with c = 1 row 2 is strictly largest; rows 1 and 2 bring columns 1 and 2."""
     D = np.array([[4.0, 0.0, 0.0], [1.0, 4.0, 0.0], [1.0 + delta, 0.0, 4.0]])
