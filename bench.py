@@ -225,7 +225,7 @@ def reference_arm(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, **PARAMS},
         "cpu_baseline": {"value": value, "unit": "columns/s", "cores": threads, "kind": "oracle",
-                         "sample": f"every {stride}th column ({ncols} of {A.n}) per step"},
+                         "sample": f"1 column in {stride} ({ncols} of {A.n}) per step"},
         "e2e": {"value": value, "unit": "columns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
