@@ -245,7 +245,9 @@ rsai_status rsai_apply(rsai_handle *h, const double *x, double *y, void *stream)
  *   dL/dB_k = -r_k z_k^T - (B_k z_k) x_k^T + 2 g_k r_k x_k^T,
  *   z_k = (B_k^T B_k)^{-1} G_M(J_k, k),  B_k = A(I_k, J_k),  x_k = m_k(J_k),
  * each QR recomputed (not stored).  The pattern is not differentiated.
- * Device pointers only.  The sum over columns has a fixed order.
+ * Device pointers only.  The sum over columns has a fixed order and uses no
+ * atomics, so the result is bit-identical from run to run (there is no
+ * separate deterministic mode).
  */
 rsai_status rsai_backward(rsai_handle *h, const double *A_val, const double *grad_M, const double *grad_rho2,
                           double *grad_A, void *stream);
