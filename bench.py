@@ -38,9 +38,24 @@ WORKLOAD = "convdiff3d_7pt_upwind_64^3_Pe5"
 # norm1, tau, 4 bins (W, W2, C, G), 3 kernels ordering the global bin's queue, 2 column-stats kernels,
 # 2 x 3 scan kernels, pool->CSC, CSC->rows, row sort
 KERNELS_PER_BUILD = 20
-# nominal CUDA-core rates (152 SMs): FP32 = 152 x 128 lanes x 2 flop x 2.07 GHz; FP64 as published for GB300
-PEAK_FP32_NOMINAL = 152 * 128 * 2 * 2.07e9
-PEAK_FP64_NOMINAL = 1.25e12
+# GB300's published FP64 rate (a side field; the roofline divides by the measured FMA-chain rate)
+PEAK_FP64_PUBLISHED = 1.25e12
+# copy bandwidth measured on this GPU type, used only when MEASURED_PEAKS.json is absent
+HBM_FALLBACK_GBS = 6800.0
+
+
+def measured_hbm_gbs():
+    """(GB/s, source) of the HBM roofline: MEASURED_PEAKS.json's copy bandwidth, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def fp32_units_peak(sms: int, sm_mhz: float) -> float:
+    """FP32 FMA rate from the unit counts: SMs x 128 lanes x 2 flop x clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6
 
 
 def log(*a):
@@ -361,6 +376,10 @@ def main():
     ph64 = {k: statistics.median(p[k] for p in phases64) for k in phases64[0]}
     f32_meas = rsai.peak_fma(False)
     f64_meas = rsai.peak_fma(True)
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    hbm_gbs, hbm_src = measured_hbm_gbs()
+    sm_max_mhz = clocks.get("sm_max_mhz") or 2070.0
 
     def roofline(stats, ph, precision):
         t = ph["bin_warp"] / 1e3
@@ -371,18 +390,21 @@ def main():
         else:
             F32 = 0.0
             F64 = stats["qr_flops"] + stats["res_flops"]
-        t32, t64 = F32 / PEAK_FP32_NOMINAL, F64 / PEAK_FP64_NOMINAL
+        t32, t64 = F32 / f32_meas, F64 / f64_meas
         pipe = "fp32" if t32 >= t64 else "fp64"
-        F, P = (F32, PEAK_FP32_NOMINAL) if pipe == "fp32" else (F64, PEAK_FP64_NOMINAL)
+        F, P = (F32, f32_meas) if pipe == "fp32" else (F64, f64_meas)
+        P_units = fp32_units_peak(sms, sm_max_mhz) if pipe == "fp32" else PEAK_FP64_PUBLISHED
         return {
             "bound": "alu", "pipe": pipe, "kernel": f"k_bin_warp<{'float' if precision != 'fp64' else 'double'}>",
             "achieved": F / t / 1e12, "peak": P / 1e12, "unit": "TFLOP/s", "frac": (F / t) / P,
             "traffic": traffic_from_profiles("k_bin_warp", precision),
-            "peak_source": "derived from unit counts and max SM clock (FP32) / published GB300 FP64 rate",
-            "peak_measured_fma_chain": (f32_meas if pipe == "fp32" else f64_meas) / 1e12,
+            "peak_source": f"measured on this GPU: FMA-chain kernel (rsai_peak_fma), {pipe.upper()}",
+            "peak_units": P_units / 1e12, "frac_of_units_peak": (F / t) / P_units,
+            "peak_units_source": (f"{sms} SMs x 128 lanes x 2 flop x {sm_max_mhz:.0f} MHz" if pipe == "fp32"
+                                  else "published GB300 FP64 rate"),
             "launch_ms": ph["bin_warp"], "flops_fp32": F32, "flops_fp64": F64,
-            "t_roof_ms": 1e3 * max(t32, t64, stats["bytes"] / 6699.2e9), "all_columns_in_kernel": all_in_w,
-            "algorithmic_bytes": stats["bytes"],
+            "t_roof_ms": 1e3 * max(t32, t64, stats["bytes"] / (hbm_gbs * 1e9)), "all_columns_in_kernel": all_in_w,
+            "algorithmic_bytes": stats["bytes"], "hbm_gbs": hbm_gbs, "hbm_source": hbm_src, "sms": sms,
         }
 
     roof32 = roofline(s32, ph32, "fp32_refine")

@@ -51,7 +51,7 @@ typedef enum {
     RSAI_ERR_CUDA = 7,          /* a CUDA runtime call failed */
     RSAI_ERR_TIMEOUT = 8,       /* a bounded device wait ran out */
     RSAI_ERR_WORKSPACE = 9,     /* a column outgrew every size bin (see rsai_stats) */
-    RSAI_ERR_BREAKDOWN = 10,    /* BiCGStab breakdown (rho = 0 or omega = 0) */
+    RSAI_ERR_BREAKDOWN = 10,    /* BiCGStab breakdown (rho = 0, rhat^T v = 0, t^T t = 0 or omega = 0) */
     RSAI_ERR_NOT_CONVERGED = 11,/* BiCGStab reached maxit */
     RSAI_ERR_NO_DEVICE = 12,    /* no CUDA device is visible */
     RSAI_ERR_TOO_LARGE = 13     /* problem larger than a fixed-size workspace */
@@ -90,8 +90,8 @@ enum {
 
 /* Flags */
 enum {
-    RSAI_FLAG_CHECKED = 1u,       /* accepted, no effect: the input checks (ranges, sortedness, the
-                                     CSR/CSC pairing) always run and report status codes */
+    /* bit 0 is reserved: the input checks (ranges, sortedness, the CSR/CSC
+       pairing) always run and report status codes, so there is no flag for them */
     RSAI_FLAG_INIT_PATTERN_A = 2u /* initial pattern J_k^(0) = rows of column k of A instead of {k}
                                      (Algorithm 1 leaves it to the user; Section 3 suggests
                                      that of I, the default, when A has a nonzero diagonal) */
@@ -296,10 +296,13 @@ rsai_status rsai_build_phase_times(rsai_handle *h, void *stream, double *ms);
  * It allocates nothing: its work vectors live in one fixed device array inside
  * the library (about 4.7 MB, held by every GPU that loads the library until the
  * process exits) and n must not exceed 65536 (else RSAI_ERR_TOO_LARGE).  The
- * array's device address is looked up on the first call on each device, so
- * make that first call before any stream capture.  Every call shares the
+ * first call on each device looks up the array's device address (and keeps it),
+ * so make that first call before any stream capture begins; after a
+ * cudaDeviceReset of a device the kept address is stale, so do not call it on
+ * that device again.  Like rsai_bicgstab it waits for the stream at every
+ * iteration to read the scalars of its stopping test.  Every call shares the
  * array: calls that overlap on the GPU race and must be ordered on one stream.
- * Same results, statuses and outputs as rsai_bicgstab.
+ * It runs rsai_bicgstab's solver code: same results, statuses and outputs.
  */
 rsai_status rsai_bicgstab_noalloc(const rsai_csr *A, const rsai_csr *M, const double *b, double *x, double rtol,
                                   int32_t maxit, int32_t *iters, double *relres, void *stream);

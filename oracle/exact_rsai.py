@@ -33,13 +33,20 @@ def _solve_normal(B, e):
     return [h[a] / G[a][a] for a in range(p)]
 
 
-def exact_rsai(A, c=3, l_max=10, eps=Fraction(3, 10), drop="fixed", tol=Fraction(1, 1000), init="identity"):
+def exact_rsai(A, c=3, l_max=10, eps=Fraction(3, 10), drop="fixed", tol=Fraction(1, 1000), init="identity",
+               trace=None):
     """Columns of M for a dense integer (or Fraction) matrix A (list of rows).
     ``init``: the initial pattern J_k^(0) (Algorithm 1), "identity" ({k})
     or "A" (the rows i with A[i][k] != 0).
 
     Returns a list of (J, m, rho2, loops) with J ascending, m exact Fractions,
     rho2 = ||r_k||^2 exact.
+
+    ``trace`` (a list, optional) receives one event list per column, in the
+    order of the algorithm: ("solve", J, kind) for every LS solve, with kind
+    "first" (the initial pattern), "grown" (J = previous J + Jhat) or
+    "dropped" (the re-solve after a drop pass), and ("rows", Rhat) for every
+    set of dominant rows taken.  Work counters can be recomputed from it.
     """
     n = len(A)
     A = [[Fraction(v) for v in row] for row in A]
@@ -48,7 +55,15 @@ def exact_rsai(A, c=3, l_max=10, eps=Fraction(3, 10), drop="fixed", tol=Fraction
     tol = Fraction(tol)
     out = []
     for k in range(n):
-        def solve(J):
+        ev = []
+        if trace is not None:
+            trace.append(ev)
+
+        def solve(J, kind):
+            ev.append(("solve", list(J), kind))
+            return _solve_plain(J)
+
+        def _solve_plain(J):
             I = sorted({i for j in J for i in range(n) if A[i][j] != 0})
             B = [[A[i][j] for j in J] for i in I]
             e = [Fraction(int(i == k)) for i in I]
@@ -67,7 +82,7 @@ def exact_rsai(A, c=3, l_max=10, eps=Fraction(3, 10), drop="fixed", tol=Fraction
             if len(keep) == len(J):
                 return J, m
             J = [J[t] for t in keep]
-            return J, solve(J)
+            return J, solve(J, "dropped")
 
         def residual(J, m):
             S = sorted({i for j in J for i in range(n) if A[i][j] != 0} | {k})
@@ -77,7 +92,7 @@ def exact_rsai(A, c=3, l_max=10, eps=Fraction(3, 10), drop="fixed", tol=Fraction
         J = [k] if init == "identity" else [i for i in range(n) if A[i][k] != 0]
         R = set()
         loops = 0
-        m = solve(J)
+        m = solve(J, "first")
         J, m = drop_pass(J, m)
         r = residual(J, m)
         rho2 = sum(v * v for v in r.values())
@@ -87,13 +102,14 @@ def exact_rsai(A, c=3, l_max=10, eps=Fraction(3, 10), drop="fixed", tol=Fraction
                 break
             cand.sort(key=lambda i: (-abs(r[i]), i))
             Rhat = cand[:c]
+            ev.append(("rows", list(Rhat)))
             R.update(Rhat)
             Jhat = sorted({j for i in Rhat for j in range(n) if A[i][j] != 0} - set(J))
             loops += 1
             if not Jhat:
                 continue
             J = sorted(set(J) | set(Jhat))
-            m = solve(J)
+            m = solve(J, "grown")
             J, m = drop_pass(J, m)
             r = residual(J, m)
             rho2 = sum(v * v for v in r.values())

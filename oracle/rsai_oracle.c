@@ -54,7 +54,9 @@
  *     4 (p-p0) sum_{j<p0} (q0-j)  +  sum_{j=p0}^{p-1} (q-j) (2 + 4 (p-j))  +  p^2
  *   a solve after a drop, and the first solve, use p0 = 0 (no previous factor);
  *   residual: 2 nnz(A(:,J)) + 2 |S|.
- *   bytes: 12 nnz(A(:,j)) + 16 each time a column j enters J,
+ *   bytes: 12 nnz(A(:,j)) + 16 once for every column j that ever enters J_k
+ *          (a column dropped and later re-entered is not counted again: the
+ *          method needs each entry of A(:,j) read once per column k),
  *          4 nnz(A(i,:)) + 16 for every dominant row i, 36 per emitted entry
  *          (12 to emit it, 24 to move it once more into CSR).
  */
@@ -294,6 +296,9 @@ static void rsai_column(const omat *A, const oparams *P, int64_t k, ocol *out, o
     int64_t capJ = 16, capR = 16;
     int32_t *J = malloc(sizeof(int32_t) * capJ);
     int32_t *Rset = malloc(sizeof(int32_t) * capR);
+    int64_t capSeen = 16;
+    int64_t nSeen = 0;
+    int32_t *seen = malloc(sizeof(int32_t) * capSeen); /* every column that has entered J, sorted */
     double *m = malloc(sizeof(double) * capJ);
     int p = 1, nR = 0, l = 0, rank = 0, solves = 0, drops = 0;
     int64_t q = 0, q0 = 0;
@@ -313,8 +318,17 @@ static void rsai_column(const omat *A, const oparams *P, int64_t k, ocol *out, o
         }
     }
 
-    /* bytes of a column of A each time it enters J */
-#define NOTE_COLUMN(j) (bytes += 12.0 * (double)(A->col_ptr[(j) + 1] - A->col_ptr[(j)]) + 16.0)
+    /* bytes of a column of A the first time it enters J */
+#define NOTE_COLUMN(j)                                                              \
+    do {                                                                            \
+        int32_t jj_ = (j);                                                          \
+        if (find(seen, nSeen, jj_) < 0) {                                           \
+            seen = grow(seen, &capSeen, nSeen + 1, sizeof(int32_t));                \
+            seen[nSeen++] = jj_;                                                    \
+            qsort(seen, (size_t)nSeen, sizeof(int32_t), cmp_i32);                   \
+            bytes += 12.0 * (double)(A->col_ptr[jj_ + 1] - A->col_ptr[jj_]) + 16.0; \
+        }                                                                           \
+    } while (0)
 
     /* Solve on J, counting work; appended = 1 if J extends the last solved J. */
 #define SOLVE(appended)                                                              \
@@ -437,6 +451,7 @@ static void rsai_column(const omat *A, const oparams *P, int64_t k, ocol *out, o
     out->res_flops = res_flops;
     out->bytes = bytes;
     free(Rset);
+    free(seen);
     (void)n;
 }
 

@@ -232,7 +232,11 @@ def bicgstab(A, M=None, b=None, rtol=1e-8, maxit=1000) -> SolveResult:
         beta = (rho / rho_old) * (alpha / omega)
         p = r + beta * (p - omega * v)
         v = Aop(Mop(p))
-        alpha = rho / float(rhat @ v)
+        rv = float(rhat @ v)
+        if rv == 0.0:  # alpha = rho / (rhat^T v) is undefined
+            status = "breakdown_alpha"
+            break
+        alpha = rho / rv
         s = r - alpha * v
         if np.linalg.norm(s) / nb < rtol:
             y = y + alpha * p

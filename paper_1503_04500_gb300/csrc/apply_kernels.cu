@@ -205,7 +205,8 @@ int bicgstab_run(int64_t n, const int64_t *Arp, const int32_t *Aci, const double
         k_bicg_s<<<blocks_for(n, T), T, 0, st>>>(n, sc, r, v, s);
         launch_dot(n, s, s, partials, sc + 7, st);
         if (!fetch(9)) { status = RSAI_ERR_CUDA; break; }
-        if (h[0] == 0.0) { status = RSAI_ERR_BREAKDOWN; break; }
+        // rho = r^T r = 0, or r^T v = 0 (alpha undefined): the recurrences break down
+        if (h[0] == 0.0 || h[4] == 0.0) { status = RSAI_ERR_BREAKDOWN; break; }
         if (sqrt(h[7]) / nb < rtol) {
             k_bicg_half<<<blocks_for(n, T), T, 0, st>>>(n, sc, p, y);
             status = RSAI_OK;

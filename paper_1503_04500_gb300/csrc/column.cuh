@@ -39,6 +39,7 @@ struct Caps {
     int small_p;   // largest |J| solved by the register-resident warp QR (0: never)
     int stage_bytes;  // shared memory for staging QR panels (global-memory bins), 0 = none
     int append;       // CTA bins: keep the factor between loops and append to it (Section 3)
+    int dcap;         // max number of distinct columns dropped from J (they are not charged again on re-entry)
 };
 
 template <typename T> struct Work {
@@ -46,6 +47,7 @@ template <typename T> struct Work {
     double *m, *r, *z, *wv;
     long long *ctr;
     int32_t *I, *S, *J, *Jn, *Rset, *buf, *buf2, *Rhat, *hkey, *hval;
+    int32_t *D;        // columns dropped from J so far, ascending
     int32_t *Ip, *Jp;  // factor position of each sorted I / J entry (Caps::append)
     T *qte;            // Q^T e_k(I) of the kept factor, factor row order (Caps::append)
     char *stage = nullptr;  // panel staging area (shared memory), not part of the carved workspace
@@ -68,6 +70,7 @@ template <typename T> struct Work {
         b += 2 * align16(sizeof(int32_t) * (size_t)c.scap);
         b += align16(sizeof(int32_t) * 32);
         b += 2 * align16(sizeof(int32_t) * (size_t)c.hcap);
+        b += align16(sizeof(int32_t) * (size_t)c.dcap);
         if (c.append) {
             b += align16(sizeof(int32_t) * (size_t)c.qcap);
             b += align16(sizeof(int32_t) * (size_t)c.pcap);
@@ -96,6 +99,7 @@ template <typename T> struct Work {
         Rhat = (int32_t *)(base + o); o += align16(sizeof(int32_t) * 32);
         hkey = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.hcap);
         hval = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.hcap);
+        D = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.dcap);
         Ip = Jp = nullptr;
         qte = nullptr;
         if (c.append) {
@@ -555,7 +559,7 @@ template <class Team, typename T> struct Column {
     const Caps &cap;
     Work<T> &w;
     int32_t k;
-    int p, q, s, nR, l;
+    int p, q, s, nR, l, nD;
     int64_t q0, p0;
     int rank_flag;
     double rho;
@@ -951,11 +955,37 @@ template <class Team, typename T> struct Column {
         return 1;
     }
 
+    // D = D u (dropped columns of J not yet in D); `kept` marks the columns
+    // that stay.  False if D outgrows its capacity.
+    template <class Kept> __device__ bool note_dropped(Kept kept) {
+        const int me = team.rank();
+        int nt = 0;
+        for (int c0 = 0; c0 < p; c0 += Team::SIZE) {
+            const int c = c0 + me;
+            const int f = (c < p) && !kept(c) && find_i32(w.D, nD, w.J[c]) < 0;
+            int tot;
+            const int pos = team.scan(f, &tot);
+            if (f) w.buf2[nt + pos] = w.J[c];
+            nt += tot;
+        }
+        team.sync();
+        if (nD + nt > cap.dcap) return false;
+        // merge by ranks (both sorted and disjoint) into buf, then back into D
+        for (int a = me; a < nD; a += Team::SIZE) w.buf[a + lower_bound_i32(w.buf2, nt, w.D[a])] = w.D[a];
+        for (int b = me; b < nt; b += Team::SIZE) w.buf[b + lower_bound_i32(w.D, nD, w.buf2[b])] = w.buf2[b];
+        team.sync();
+        nD += nt;
+        for (int a = me; a < nD; a += Team::SIZE) w.D[a] = w.buf[a];
+        team.sync();
+        return true;
+    }
+
     // Eq. 4.3: drop |m_j| <= tau, keep at least the largest, re-solve once.
     // Magnitudes are compared as ordered integer keys (exact).
-    // Returns true if J lost entries (the caller re-solves once).
-    __device__ bool drop() {
-        if (P.drop_mode == RSAI_DROP_NONE) return false;
+    // Returns 1 if J lost entries (the caller re-solves once), 0 if not, -1
+    // if the set of dropped columns outgrows this bin.
+    __device__ int drop() {
+        if (P.drop_mode == RSAI_DROP_NONE) return 0;
         const int me = team.rank();
         const int blk = P.col_block ? P.col_block[k] : 0;
         const double tau = (P.drop_mode == RSAI_DROP_ADAPTIVE) ? P.eps / ((double)p * P.norm1[blk]) : P.tau_fixed[blk];
@@ -969,16 +999,18 @@ template <class Team, typename T> struct Column {
             if (dom_before(a, c, ba, bi)) { ba = a; bi = c; }
         }
         const int keep_total = team.sum(nkeep);
-        if (keep_total == p) return false;
+        if (keep_total == p) return 0;
         if (keep_total == 0) {
             team.argmax(ba, bi);
-            if (p == 1) return false;
+            if (p == 1) return 0;
+            if (!note_dropped([&](int c) { return c == bi; })) return -1;
             int32_t jb = w.J[bi];
             team.sync();
             if (me == 0) w.J[0] = jb;
             p = 1;
             team.sync();
         } else {
+            if (!note_dropped([&](int c) { return abskey(w.m[c]) > tk; })) return -1;
             int base = 0;
             for (int c0 = 0; c0 < p; c0 += Team::SIZE) {
                 int c = c0 + me;
@@ -994,7 +1026,7 @@ template <class Team, typename T> struct Column {
             team.sync();
         }
         c_drops += 1;
-        return true;
+        return 1;
     }
 
     // Top-c dominant rows of S \ R (Algorithm 1, Eq. 3.2) into w.Rhat; returns
@@ -1141,12 +1173,13 @@ template <class Team, typename T> struct Column {
         return true;
     }
 
-    // algorithmic bytes of columns entering J: 12 per nonzero + 16 of pointers
+    // algorithmic bytes of columns entering J for the first time: 12 per
+    // nonzero + 16 of pointers (a column dropped earlier was charged then)
     __device__ void note_bytes_columns(int from, int count, const int32_t *list) {
         long long b = 0;
         for (int t = from + team.rank(); t < from + count; t += Team::SIZE) {
             int32_t j = list[t];
-            b += 12 * (A.col_ptr[j + 1] - A.col_ptr[j]) + 16;
+            if (find_i32(w.D, nD, j) < 0) b += 12 * (A.col_ptr[j + 1] - A.col_ptr[j]) + 16;
         }
         c_bytes += team.sum(b);
     }
@@ -1156,7 +1189,7 @@ template <class Team, typename T> struct Column {
 
     // J = Jk (sorted, length pk): false if it does not fit this bin
     __device__ bool load_pattern(const int32_t *Jk, int pk) {
-        p = pk; q = 0; s = 0; nR = 0; l = 0; q0 = 0; p0 = 0; rank_flag = 0; rho = 0.0;
+        p = pk; q = 0; s = 0; nR = 0; l = 0; nD = 0; q0 = 0; p0 = 0; rank_flag = 0; rho = 0.0;
         if constexpr (!std::is_same<Team, WarpTeam>::value) fact_valid = false;
         c_qr = c_res = c_ref = c_ref64 = c_bytes = 0;
         c_solves = c_drops = c_pmax = c_qmax = 0;
@@ -1302,7 +1335,7 @@ template <class Team, typename T> struct Column {
 
     __device__ int run() {
         const int me = team.rank();
-        p = 1; q = 0; s = 0; nR = 0; l = 0; q0 = 0; p0 = 0; rank_flag = 0; rho = 0.0;
+        p = 1; q = 0; s = 0; nR = 0; l = 0; nD = 0; q0 = 0; p0 = 0; rank_flag = 0; rho = 0.0;
         if constexpr (!std::is_same<Team, WarpTeam>::value) fact_valid = false;
         c_qr = c_res = c_ref = c_ref64 = c_bytes = 0;
         c_solves = c_drops = c_pmax = c_qmax = 0;
@@ -1334,7 +1367,10 @@ template <class Team, typename T> struct Column {
                 }
                 first = false;
                 append = false;
-                if (pass == 1 || !drop()) break;
+                if (pass == 1) break;
+                const int dr = drop();
+                if (dr < 0) return COL_OVERFLOW;
+                if (dr == 0) break;
             }
             residual();
             bool grown = false;

@@ -108,7 +108,12 @@ constexpr int kScalars = kPartial + kStatBlocks;
 
 double *dword(const rsai_handle *h, int at) { return reinterpret_cast<double *>(h->dscal + at); }
 
-int cuda_status(cudaError_t e) { return e == cudaSuccess ? RSAI_OK : RSAI_ERR_CUDA; }
+// a failed allocation inside a launch sequence (the global bin's slab) comes
+// back as cudaErrorMemoryAllocation: it is an OOM, not a CUDA fault
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return RSAI_OK;
+    return e == cudaErrorMemoryAllocation ? RSAI_ERR_OOM : RSAI_ERR_CUDA;
+}
 
 // The library's own stream-ordered pool on the current device.  Up to
 // kPoolKeep bytes that handles give back stay mapped in it, so that building
@@ -241,7 +246,10 @@ cudaError_t enqueue_bins(rsai_handle *h, int mode, const DevA &A, const Frozen &
     if (ev) cudaEventRecord(ev[2], st);
     e = launch_bin_block(mode, fp32, h->grid_c, A, P, h->capC, QC, O, F, gctr, false, nullptr, 0, 1, st);
     if (e != cudaSuccess) return e;
-    if (before_global && before_global(h, st) != RSAI_OK) return cudaErrorMemoryAllocation;
+    if (before_global) {
+        const int hr = before_global(h, st);
+        if (hr != RSAI_OK) return hr == RSAI_ERR_OOM ? cudaErrorMemoryAllocation : cudaErrorUnknown;
+    }
     // the columns that reached the global bin, largest first (grids cover n;
     // the device-side count bounds the work)
     cudaMemsetAsync(h->cost_hist, 0, sizeof(uint32_t) * kCostBuckets, st);
@@ -342,16 +350,16 @@ int plan_bins(rsai_handle *h) {
     int dev = h->device, max_optin = 0;
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int rneed = std::max(64, h->params.c * std::max(1, h->params.l_max));
-    h->capW = Caps{64, 32, 256, 64, 64 * 32, 64, h->tuning.small_qr_max_p, 0};
+    h->capW = Caps{64, 32, 256, 64, 64 * 32, 64, h->tuning.small_qr_max_p, 0, 0, 64};
     int occ = occupancy_bin_warp(fp32, h->tuning.warp_bin_warps, h->capW);
     if (occ < 1) return RSAI_ERR_CUDA;
     if (h->tuning.warp_bin_ctas_per_sm > 0) occ = std::min(occ, h->tuning.warp_bin_ctas_per_sm);
     h->grid_w = h->sms * occ;
     // bin W2: the warp bin's algorithm for |I| <= 128 (B 128 x 32), fewer warps per SM
-    h->capW2 = Caps{128, 32, 512, 64, 128 * 32, 64, h->tuning.small_qr_max_p, 0};
+    h->capW2 = Caps{128, 32, 512, 64, 128 * 32, 64, h->tuning.small_qr_max_p, 0, 0, 128};
     if (plan_w2(h, fp32) != RSAI_OK) return RSAI_ERR_CUDA;
     // bin C: shared-memory workspace as large as the opt-in limit allows
-    Caps c{1024, 256, 4096, std::min(rneed * 2, 2048), 0, 0, 0, 0, 1};
+    Caps c{1024, 256, 4096, std::min(rneed * 2, 2048), 0, 0, 0, 0, 1, 1024};
     size_t base = fp32 ? work_bytes<float>(c) : work_bytes<double>(c);
     size_t avail = (size_t)max_optin - 2048;
     if (base >= avail) return RSAI_ERR_CUDA;
@@ -361,7 +369,7 @@ int plan_bins(rsai_handle *h) {
     if (occ < 1) return RSAI_ERR_CUDA;
     h->grid_c = h->sms * occ;
     // bin G: a global-memory slab per CTA, one CTA per SM
-    h->capG = Caps{32768, 4096, 131072, 8192, (int64_t)1 << 24, 0, 0, max_optin - 2048, 1};
+    h->capG = Caps{32768, 4096, 131072, 8192, (int64_t)1 << 24, 0, 0, max_optin - 2048, 1, 32768};
     h->gstride = ((fp32 ? work_bytes<float>(h->capG) : work_bytes<double>(h->capG)) + 255) & ~size_t(255);
     h->grid_g = 1;  // sized by the first build (size_global_slab)
     return RSAI_OK;
@@ -415,7 +423,7 @@ rsai_status rsai_params_check(const rsai_params *p) {
     if (!(p->tol >= 0.0) || !std::isfinite(p->tol)) return RSAI_ERR_INVALID_ARG;
     if (p->precision != RSAI_FP64 && p->precision != RSAI_FP32_REFINE) return RSAI_ERR_INVALID_ARG;
     if (!(p->tie_band >= 0.0) || !(p->tie_band < 1.0)) return RSAI_ERR_INVALID_ARG;
-    if (p->flags & ~(uint32_t)(RSAI_FLAG_CHECKED | RSAI_FLAG_INIT_PATTERN_A)) return RSAI_ERR_INVALID_ARG;
+    if (p->flags & ~(uint32_t)RSAI_FLAG_INIT_PATTERN_A) return RSAI_ERR_INVALID_ARG;
     return RSAI_OK;
 }
 
@@ -465,21 +473,22 @@ int build_common(rsai_handle *h, cudaStream_t st) {
     TRY(dalloc(h, &h->norm1_arr, h->nblocks, st));
     TRY(dalloc(h, &h->tau_arr, h->nblocks, st));
     // ---- validation of A (device kernels, error codes) ----
+    // One pass on the stream, one read of the first error: each check after
+    // the pointer checks returns at once if an earlier one set the error word,
+    // so it never follows an index that was not checked.
     {
         int32_t herr = 0;
-        auto step = [&](auto launch) -> int {
-            cudaMemsetAsync(h->err, 0, sizeof(int32_t), st);
-            launch();
-            if (cudaMemcpyAsync(&herr, h->err, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-                return RSAI_ERR_CUDA;
-            if (cudaStreamSynchronize(st) != cudaSuccess) return RSAI_ERR_CUDA;
-            return herr;
-        };
-        TRY(step([&] { k_check_ptr<<<blocks(n + 1, 256), 256, 0, st>>>(h->row_ptr, n, nnz, h->err); }));
-        TRY(step([&] { k_check_ptr<<<blocks(n + 1, 256), 256, 0, st>>>(h->col_ptr, n, nnz, h->err); }));
-        TRY(step([&] { k_check_idx<<<blocks(n, 256), 256, 0, st>>>(h->row_ptr, h->col_idx, n, h->err, 0); }));
-        TRY(step([&] { k_check_idx<<<blocks(n, 256), 256, 0, st>>>(h->col_ptr, h->row_idx, n, h->err, 1); }));
-        TRY(step([&] { k_csc_map<<<blocks(n, 256), 256, 0, st>>>(dev_a(h), h->csc_to_csr, h->err); }));
+        cudaMemsetAsync(h->err, 0, sizeof(int32_t), st);
+        k_check_ptr<<<blocks(n + 1, 256), 256, 0, st>>>(h->row_ptr, n, nnz, h->err);
+        k_check_ptr<<<blocks(n + 1, 256), 256, 0, st>>>(h->col_ptr, n, nnz, h->err);
+        k_check_idx<<<blocks(n, 256), 256, 0, st>>>(h->row_ptr, h->col_idx, n, h->err, 0);
+        k_check_idx<<<blocks(n, 256), 256, 0, st>>>(h->col_ptr, h->row_idx, n, h->err, 1);
+        k_csc_map<<<blocks(n, 256), 256, 0, st>>>(dev_a(h), h->csc_to_csr, h->err);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(&herr, h->err, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return RSAI_ERR_CUDA;
+        TRY(herr);
     }
     TRY(plan_bins(h));
     // ---- buffers of the build sequence ----
@@ -783,9 +792,14 @@ rsai_status rsai_get_stats(rsai_handle *h, void *stream, rsai_stats *out) {
     cudaStream_t st = (cudaStream_t)stream;
     unsigned long long s[kCounts + 2];
     int32_t herr = 0;
-    if (cudaMemcpyAsync(s, h->dscal, sizeof(s), cudaMemcpyDeviceToHost, st) != cudaSuccess) return RSAI_ERR_CUDA;
-    cudaMemcpyAsync(&herr, h->err, sizeof(herr), cudaMemcpyDeviceToHost, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return RSAI_ERR_CUDA;
+    std::vector<double> nb((size_t)h->nblocks);
+    // every read on the caller's stream, one wait
+    if (cudaMemcpyAsync(s, h->dscal, sizeof(s), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&herr, h->err, sizeof(herr), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(nb.data(), h->norm1_arr, sizeof(double) * nb.size(), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return RSAI_ERR_CUDA;
     auto dbl = [&](int at) {
         double v;
         memcpy(&v, &s[at], sizeof(v));
@@ -796,8 +810,6 @@ rsai_status rsai_get_stats(rsai_handle *h, void *stream, rsai_stats *out) {
     out->n = h->n;
     out->nnz_A = h->nnz;
     {
-        std::vector<double> nb((size_t)h->nblocks);
-        cudaMemcpy(nb.data(), h->norm1_arr, sizeof(double) * nb.size(), cudaMemcpyDeviceToHost);
         double mx = 0.0;
         for (double v : nb) mx = std::max(mx, v);
         out->norm1_A = mx;

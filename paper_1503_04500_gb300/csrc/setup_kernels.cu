@@ -18,9 +18,11 @@ __global__ void k_check_ptr(const int64_t *ptr, int64_t n, int64_t nnz, int32_t 
     if (i < n && ptr[i] > ptr[i + 1]) set_error(err, RSAI_ERR_INDEX_RANGE);
 }
 
+// Runs after k_check_ptr on the same stream: if a pointer array was found
+// invalid (err set), its entries are not used as indices.
 __global__ void k_check_idx(const int64_t *ptr, const int32_t *idx, int64_t n, int32_t *err, int empty_is_error) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || *(volatile int32_t *)err != 0) return;
     int64_t a = ptr[i], b = ptr[i + 1];
     if (empty_is_error && a == b) set_error(err, RSAI_ERR_EMPTY_COLUMN);
     for (int64_t e = a; e < b; ++e) {
@@ -30,10 +32,12 @@ __global__ void k_check_idx(const int64_t *ptr, const int32_t *idx, int64_t n, i
     }
 }
 
-// CSR position of every CSC entry; checks that both describe the same matrix
+// CSR position of every CSC entry; checks that both describe the same matrix.
+// Runs after the pointer and index checks on the same stream and does nothing
+// if they found an error (its indices would not be safe to follow).
 __global__ void k_csc_map(DevA A, int64_t *csc_to_csr, int32_t *err) {
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= A.n) return;
+    if (j >= A.n || *(volatile int32_t *)err != 0) return;
     for (int64_t e = A.col_ptr[j]; e < A.col_ptr[j + 1]; ++e) {
         int32_t i = A.row_idx[e];
         int64_t lo = A.row_ptr[i];

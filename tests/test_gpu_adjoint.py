@@ -113,27 +113,27 @@ def test_theta_gradient_central_differences(precision, rtol):
 def test_refit_and_backward_across_all_bins(precision, rtol):
     """Refit and adjoint on a power-law matrix whose columns land in every bin
     (warp, second warp, CTA with shared memory, CTA with a global slab), against
-    the oracle on the oracle's own pattern (which the FP64 build reproduces)."""
+    the oracle on the handle's own frozen pattern.  The FP64 build reproduces
+    the oracle's pattern bit for bit; an FP32+refine build may differ from it on
+    a few columns, and every column is checked all the same."""
     A = gen.powerlaw(2000, seed=17, dmax=100)
     kw = dict(c=5, l_max=8, eps=0.4, tol=1e-3, drop="fixed")
     ref = oracle.build(A, **kw)
-    colptr, Mrows = ref.colptr.astype(np.int64), ref.rows.astype(np.int32)
     dA = rsai.DeviceMatrix.from_host(A)
-    h = rsai.build(dA, precision="fp64", **kw)
+    h = rsai.build(dA, precision=precision, **kw)
     st = h.stats()
     assert st["cols_bin"][1] > 0 and st["cols_bin"][2] > 0
-    orp, oci, _ = ref.csr()
     rp, ci, va = (t.cpu().numpy() for t in h.M())
-    assert np.array_equal(rp, orp) and np.array_equal(ci, oci)
-    if precision != "fp64":
-        h.free()
-        h = rsai.build(dA, precision=precision, **kw)
-        rp2, ci2, _ = (t.cpu().numpy() for t in h.M())
-        if not (np.array_equal(rp2, orp) and np.array_equal(ci2, oci)):
-            pytest.skip("FP32+refine pattern differs from FP64 on this matrix (allowed for 1% of columns)")
-    # CSR position of every CSC entry of M
+    if precision == "fp64":
+        orp, oci, _ = ref.csr()
+        assert np.array_equal(rp, orp) and np.array_equal(ci, oci)
+    # the handle's frozen pattern, column-wise, and the CSR position of every CSC entry of M
     rows = np.repeat(np.arange(A.n), np.diff(rp))
     csc_pos = np.lexsort((rows, ci))
+    colptr = np.zeros(A.n + 1, np.int64)
+    np.add.at(colptr, ci.astype(np.int64) + 1, 1)
+    colptr = np.cumsum(colptr)
+    Mrows = rows[csc_pos].astype(np.int32)
     vals2 = A.val * (1.0 + 0.05 * np.sin(np.arange(A.nnz)))
     mv, rho2 = h.refit(torch.as_tensor(vals2, device="cuda"))
     ov, orho2 = oracle.refit(A.with_values(vals2), colptr, Mrows)

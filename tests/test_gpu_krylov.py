@@ -41,21 +41,32 @@ def test_spmv_primitives_match_numpy():
     np.testing.assert_array_equal(y, y2)
 
 
-def _oracle_pattern(ref):
-    return ref.colptr.astype(np.int64), ref.rows.astype(np.int32)
+def _pattern_of(h, n):
+    """The handle's frozen pattern of M, column-wise (colptr, rows)."""
+    rp, ci, _ = (t.cpu().numpy() for t in h.M())
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    order = np.lexsort((rows, ci))
+    colptr = np.zeros(n + 1, np.int64)
+    np.add.at(colptr, ci.astype(np.int64) + 1, 1)
+    return np.cumsum(colptr), rows[order].astype(np.int32)
 
 
-def test_loss_gradient_matches_oracle_reference():
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-7), ("fp32_refine", 1e-5)])
+def test_loss_gradient_matches_oracle_reference(precision, rtol):
+    """d||b - A M y_5||^2 / dA on the 12^2 parametric problem against a CPU
+    reference: the oracle's FP64 values and LS adjoint of M(A) on the handle's
+    frozen pattern (the oracle's own pattern for the FP64 build), with dense
+    torch autograd through the five BiCGStab iterations."""
     P = gen.parametric2d(12, (30.0, 10.0))
     A = P.base
     iters = 5
-    ref = oracle.build(A, **KW)
-    colptr, Mrows = _oracle_pattern(ref)
     dA = rsai.DeviceMatrix.from_host(A)
-    h = rsai.build(dA, precision="fp64", **KW)
-    orp, oci, _ = ref.csr()
-    rp, ci, _ = (t.cpu().numpy() for t in h.M())
-    assert np.array_equal(rp, orp) and np.array_equal(ci, oci)  # same pattern as the oracle's
+    h = rsai.build(dA, precision=precision, **KW)
+    colptr, Mrows = _pattern_of(h, A.n)
+    if precision == "fp64":
+        ref = oracle.build(A, **KW)
+        np.testing.assert_array_equal(colptr, ref.colptr)
+        np.testing.assert_array_equal(Mrows, ref.rows)
     b_np = gen.ones_rhs(A)
 
     A_val = dA.val.clone().requires_grad_(True)
@@ -79,33 +90,67 @@ def test_loss_gradient_matches_oracle_reference():
     L.backward()
     g_ref = At.grad.numpy() + oracle.backward(A, colptr, Mrows, Mt.grad.numpy(), np.zeros(n))
 
-    np.testing.assert_allclose(loss.item(), L.item(), rtol=1e-9)
-    np.testing.assert_allclose(g_gpu, g_ref, rtol=1e-7, atol=1e-9 * np.abs(g_ref).max())
+    np.testing.assert_allclose(loss.item(), L.item(), rtol=10 * rtol)
+    np.testing.assert_allclose(g_gpu, g_ref, rtol=rtol, atol=1e-2 * rtol * np.abs(g_ref).max())
+    h.free()
 
 
-def test_theta_gradient_at_full_size_central_differences():
-    """Parametric 256^2 problem, y_20: dL/dtheta by autograd through the GPU
-    kernels against central differences of the same (frozen-pattern) loss."""
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-6), ("fp32_refine", 1e-4)])
+def test_theta_gradient_at_full_size_central_differences(precision, rtol):
+    """Parametric 256^2 problem (n = 65536), loss_2 = ||b - A M y_20||^2 with
+    y_20 from 20 BiCGStab iterations: dL/dtheta by autograd through the GPU
+    kernels (FP64 or FP32+refine) against central differences, with step
+    h = 1e-6 * theta_1, of the FP64 loss that the oracle evaluates on the same
+    frozen pattern (its refit of M(theta), then its BiCGStab with the stopping
+    test disabled for exactly 20 iterations).
+
+    The oracle's loss carries rounding noise (about 5e-10 of L, from the 20
+    Krylov iterations), which a step this small turns into an error of about
+    1e-3 of the smaller derivative.  So the derivative is the least-squares
+    slope of L at theta + j h e_i, j = -3..3, and the check allows
+    rtol * |slope| plus four standard errors of that slope, taken from the
+    residuals of the fit."""
     P = gen.parametric2d(256, (30.0, 10.0))
     A = P.base
     dA = rsai.DeviceMatrix.from_host(A)
-    h = rsai.build(dA, precision="fp64", **KW)
+    h = rsai.build(dA, precision=precision, **KW)
     patA, patM = Pattern.of_matrix(A), Pattern.of_M(h)
-    b = _dev(gen.ones_rhs(A))
+    colptr, Mrows = _pattern_of(h, A.n)
+    b_np = gen.ones_rhs(A)
+    b = _dev(b_np)
     Lt, C1, C2 = _dev(P.L), _dev(P.C[0]), _dev(P.C[1])
 
-    def loss(theta):
-        return preconditioned_solve_loss(Lt + theta[0] * C1 + theta[1] * C2, h, patA, patM, b, 20)
-
     theta = torch.tensor(P.theta, dtype=torch.float64, device="cuda", requires_grad=True)
-    L0 = loss(theta)
+    L0 = preconditioned_solve_loss(Lt + theta[0] * C1 + theta[1] * C2, h, patA, patM, b, 20)
     g = torch.autograd.grad(L0, theta)[0].cpu().numpy()
     assert np.isfinite(L0.item()) and L0.item() > 0
-    with torch.no_grad():
-        for i in range(2):
-            step = 1e-4 * P.theta[i]
-            e = torch.zeros(2, dtype=torch.float64, device="cuda")
-            e[i] = step
-            fd = (loss(theta + e) - loss(theta - e)).item() / (2 * step)
-            assert abs(g[i] - fd) <= 1e-4 * abs(fd), (i, g[i], fd)
+
+    nb = float(np.linalg.norm(b_np))
+    colk = np.repeat(np.arange(A.n), np.diff(colptr))
+    order = np.lexsort((colk, Mrows))
+    Mrp = np.zeros(A.n + 1, np.int64)
+    np.add.at(Mrp, Mrows.astype(np.int64) + 1, 1)
+    Mrp = np.cumsum(Mrp)
+
+    def loss_oracle(th):
+        At = A.with_values(P.values(th))
+        mv, _ = oracle.refit(At, colptr, Mrows)
+        sol = oracle.bicgstab(At, (Mrp, colk[order].astype(np.int32), mv[order]), b_np, rtol=0.0, maxit=20)
+        assert sol.iters == 20
+        return (sol.relres_true * nb) ** 2
+
+    np.testing.assert_allclose(L0.item(), loss_oracle(list(P.theta)), rtol=1e-8 if precision == "fp64" else 1e-5)
+    step = 1e-6 * P.theta[0]
+    js = np.arange(-3, 4, dtype=np.float64)
+    for i in range(2):
+        Ls = []
+        for j in js:
+            th = list(P.theta)
+            th[i] += j * step
+            Ls.append(loss_oracle(th))
+        Ls = np.array(Ls)
+        slope = float(js @ Ls) / (step * float(js @ js))
+        resid = Ls - Ls.mean() - slope * step * js
+        stderr = float(np.sqrt((resid @ resid) / (len(js) - 2))) / (step * float(np.sqrt(js @ js)))
+        assert abs(g[i] - slope) <= rtol * abs(slope) + 4.0 * stderr, (precision, i, g[i], slope, stderr)
     h.free()
