@@ -10,6 +10,12 @@ residuals and norms are exact, ties are exact, and the tests ||r|| <= eps and
 Readings are the same as the FP64 oracle's (S = I u {k}, drop once after every
 solve then re-solve, keep-one, ties by lowest index, excluded rows R, empty
 Jhat loops counted); with exact arithmetic no tie band is needed.
+
+With ``select="spai"`` the new indices are SPAI's most profitable ones
+(Section 2, Eqs. 2.5-2.7): the candidates are the nonzero columns of the rows
+where r != 0, less J, ranked by s_j = (r^T A e_j)^2 / ||A e_j||^2 exactly
+(the largest s_j is the smallest rho_j), ties by lowest j; no candidate ends
+the column.
 """
 from __future__ import annotations
 
@@ -34,7 +40,7 @@ def _solve_normal(B, e):
 
 
 def exact_rsai(A, c=3, l_max=10, eps=Fraction(3, 10), drop="fixed", tol=Fraction(1, 1000), init="identity",
-               trace=None):
+               trace=None, select="rsai"):
     """Columns of M for a dense integer (or Fraction) matrix A (list of rows).
     ``init``: the initial pattern J_k^(0) (Algorithm 1), "identity" ({k})
     or "A" (the rows i with A[i][k] != 0).
@@ -46,7 +52,8 @@ def exact_rsai(A, c=3, l_max=10, eps=Fraction(3, 10), drop="fixed", tol=Fraction
     order of the algorithm: ("solve", J, kind) for every LS solve, with kind
     "first" (the initial pattern), "grown" (J = previous J + Jhat) or
     "dropped" (the re-solve after a drop pass), and ("rows", Rhat) for every
-    set of dominant rows taken.  Work counters can be recomputed from it.
+    set of dominant rows taken (RSAI), or ("spai", L, candidates, added) for
+    every SPAI selection.  Work counters can be recomputed from it.
     """
     n = len(A)
     A = [[Fraction(v) for v in row] for row in A]
@@ -97,6 +104,23 @@ def exact_rsai(A, c=3, l_max=10, eps=Fraction(3, 10), drop="fixed", tol=Fraction
         r = residual(J, m)
         rho2 = sum(v * v for v in r.values())
         while rho2 > eps * eps and loops < l_max:
+            if select == "spai":
+                L = sorted(i for i, v in r.items() if v != 0)
+                if not L:
+                    break
+                N = sorted({j for i in L for j in range(n) if A[i][j] != 0} - set(J))
+                if not N:
+                    break
+                score = {j: sum(r[i] * A[i][j] for i in r) ** 2 / sum(A[i][j] ** 2 for i in range(n)) for j in N}
+                add = sorted(N, key=lambda j: (-score[j], j))[:c]
+                ev.append(("spai", L, N, sorted(add)))
+                loops += 1
+                J = sorted(set(J) | set(add))
+                m = solve(J, "grown")
+                J, m = drop_pass(J, m)
+                r = residual(J, m)
+                rho2 = sum(v * v for v in r.values())
+                continue
             cand = [i for i, v in r.items() if v != 0 and i not in R]
             if not cand:
                 break

@@ -11,7 +11,8 @@
  * follows Algorithm 1 in the paper's order.
  *
  * What it computes, per column k (Section 2 Eq. 2.2-2.4, Section 3 Algorithm 1,
- * Section 4 Eq. 4.3):
+ * Section 4 Eq. 4.3; or, with select_mode SPAI, the selection of Section 2
+ * Eqs. 2.5-2.7 in place of the dominant rows):
  *   J = J0(k), R = {}, l = 0                         (initial pattern)
  *     J0(k) = {k} (the pattern of I, the paper's usual choice) or the
  *     pattern of column k of A (init_mode 1)
@@ -23,6 +24,14 @@
  *     Jhat = cols(A(Rhat,:)) \ J                     (new columns)
  *     l = l + 1; if Jhat empty: continue             (empty Jhat)
  *     J += Jhat; Solve(J); Drop(J); r, rho           (update of m_k, Eq. 4.3)
+ *   SPAI selection (select_mode 1) replaces the three selection lines:
+ *     L = {i in S : |r_i| > band}                    (Eq. 2.5: rows where r != 0)
+ *     N = nonzero columns of A(L,:); Jhat = N \ J     (candidates, Eq. 2.5)
+ *     if Jhat empty: stop
+ *     rho_j^2 = ||r||^2 - (r^T A e_j)^2 / ||A e_j||^2 (Eq. 2.7, from Eq. 2.6)
+ *     take the c candidates with the smallest rho_j, i.e. the largest
+ *     s_j = (r^T A e_j)^2 / ||A e_j||^2, by (s_j desc, j asc) with a tie band
+ *     of tie_band * ||r||^2 (s_j <= ||r||^2); l = l + 1
  *
  * Readings of points the paper leaves open (each is restated in the design
  * notes of the repository):
@@ -46,6 +55,10 @@
  *     raises l before it returns to its loop test).
  *   - Rank: if |R_jj| <= q*u*||B||_F the column is flagged RANK and that
  *     component of m is set to zero.
+ *   - SPAI: no set of excluded rows (every row with r_i != 0 feeds the
+ *     candidates each loop); a loop with no candidate left ends the column
+ *     without counting (it could add nothing later either); candidates with
+ *     s_j = 0 (no improvement) may still be taken when fewer than c do better.
  *
  * Algorithmic work counters (the method's own work, with the paper's QR
  * update rather than this file's refactoring; Section 3 "update ... as in
@@ -54,6 +67,9 @@
  *     4 (p-p0) sum_{j<p0} (q0-j)  +  sum_{j=p0}^{p-1} (q-j) (2 + 4 (p-j))  +  p^2
  *   a solve after a drop, and the first solve, use p0 = 0 (no previous factor);
  *   residual: 2 nnz(A(:,J)) + 2 |S|.
+ *   SPAI selection: 4 nnz(A e_j) + 3 per candidate j per loop (its dot
+ *   product with r, its squared norm, Eq. 2.7); bytes 4 nnz(A(i,:)) + 16 per
+ *   row of L and 12 nnz(A e_j) + 16 per candidate, each loop.
  *   bytes: 12 nnz(A(:,j)) + 16 once for every column j that ever enters J_k
  *          (a column dropped and later re-entered is not counted again: the
  *          method needs each entry of A(:,j) read once per column k),
@@ -69,6 +85,7 @@
 #endif
 
 enum { DROP_NONE = 0, DROP_ADAPTIVE = 1, DROP_FIXED = 2 };
+enum { SELECT_RSAI = 0, SELECT_SPAI = 1 };
 enum { FLAG_CONVERGED = 1, FLAG_RANK = 2, FLAG_NONFINITE = 4 };
 
 typedef struct {
@@ -80,6 +97,7 @@ typedef struct {
 typedef struct {
     int32_t c, l_max, drop_mode, init_mode;  /* init_mode: 0 = pattern of I, 1 = pattern of A */
     double eps, tol, tie_band, norm1;
+    int32_t select_mode;                     /* SELECT_RSAI (dominant rows) or SELECT_SPAI */
 } oparams;
 
 /* one finished column of M */
@@ -90,7 +108,7 @@ typedef struct {
     double rho;
     int32_t loops, flags, solves, drops;
     int32_t p_max, q_max; /* largest LS problem met */
-    double qr_flops, res_flops, bytes;
+    double qr_flops, res_flops, bytes, sel_flops;
 } ocol;
 
 typedef struct {
@@ -304,7 +322,7 @@ static void rsai_column(const omat *A, const oparams *P, int64_t k, ocol *out, o
     int64_t q = 0, q0 = 0;
     int p0 = 0, pmax = 1;
     int64_t qmax = 0;
-    double qr_flops = 0.0, res_flops = 0.0, bytes = 0.0, rho = 0.0, nnzJ = 0.0;
+    double qr_flops = 0.0, res_flops = 0.0, bytes = 0.0, rho = 0.0, nnzJ = 0.0, sel_flops = 0.0;
     J[0] = (int32_t)k;
     if (P->init_mode == 1) {
         /* Algorithm 1 started from the initial pattern of A: J = rows of A(:,k) */
@@ -368,6 +386,82 @@ static void rsai_column(const omat *A, const oparams *P, int64_t k, ocol *out, o
     res_flops += 2.0 * nnzJ + 2.0 * (double)s;
 
     while (rho > P->eps && l < P->l_max) {
+        if (P->select_mode == SELECT_SPAI) {
+            /* L = rows of S where r != 0 (beyond the band), Eq. 2.5 */
+            double rinf = 0.0, rr = 0.0;
+            for (int64_t i = 0; i < s; ++i) {
+                if (fabs(w->r[i]) > rinf) rinf = fabs(w->r[i]);
+                rr += w->r[i] * w->r[i];
+            }
+            double band = P->tie_band * rinf;
+            int64_t tot = 0, nL = 0;
+            for (int64_t i = 0; i < s; ++i)
+                if (fabs(w->r[i]) > band) {
+                    int32_t row = w->S[i];
+                    tot += A->row_ptr[row + 1] - A->row_ptr[row];
+                    bytes += 4.0 * (double)(A->row_ptr[row + 1] - A->row_ptr[row]) + 16.0;
+                    ++nL;
+                }
+            if (nL == 0) break;
+            /* N = nonzero columns of A(L,:); Jhat = N \ J */
+            w->tmp = grow(w->tmp, &w->capT, tot + 1, sizeof(int32_t));
+            int64_t nj = 0;
+            for (int64_t i = 0; i < s; ++i)
+                if (fabs(w->r[i]) > band) {
+                    int32_t row = w->S[i];
+                    for (int64_t e = A->row_ptr[row]; e < A->row_ptr[row + 1]; ++e)
+                        if (find(J, p, A->col_idx[e]) < 0) w->tmp[nj++] = A->col_idx[e];
+                }
+            nj = sort_unique(w->tmp, nj);
+            if (nj == 0) break; /* no candidate: nothing can be added */
+            /* s_j = (r^T A e_j)^2 / ||A e_j||^2 (Eq. 2.7: rho_j^2 = ||r||^2 - s_j) */
+            keyed *cand = malloc(sizeof(keyed) * (size_t)nj);
+            for (int64_t t = 0; t < nj; ++t) {
+                int32_t j = w->tmp[t];
+                double dot = 0.0, nrm = 0.0;
+                for (int64_t e = A->col_ptr[j]; e < A->col_ptr[j + 1]; ++e) {
+                    int64_t pos = find(w->S, s, A->row_idx[e]);
+                    if (pos >= 0) dot += w->r[pos] * A->cval[e];
+                    nrm += A->cval[e] * A->cval[e];
+                }
+                double len = (double)(A->col_ptr[j + 1] - A->col_ptr[j]);
+                sel_flops += 4.0 * len + 3.0;
+                bytes += 12.0 * len + 16.0;
+                cand[t].a = (nrm > 0.0) ? dot * dot / nrm : 0.0;
+                cand[t].i = j;
+            }
+            /* the c largest s_j, ties by lowest j within tie_band * ||r||^2 */
+            int c = P->c < 64 ? P->c : 64;
+            int32_t add[64];
+            int na = 0;
+            if (nj <= c) {
+                for (int64_t t = 0; t < nj; ++t) add[na++] = cand[t].i;
+            } else {
+                double sband = P->tie_band * rr;
+                qsort(cand, (size_t)nj, sizeof(keyed), cmp_dom);
+                double v = cand[c - 1].a;
+                for (int64_t t = 0; t < nj; ++t) if (cand[t].a > v + sband) add[na++] = cand[t].i;
+                keyed *tie = malloc(sizeof(keyed) * (size_t)nj);
+                int64_t nt = 0;
+                for (int64_t t = 0; t < nj; ++t)
+                    if (cand[t].a >= v - sband && cand[t].a <= v + sband) tie[nt++] = cand[t];
+                qsort(tie, (size_t)nt, sizeof(keyed), cmp_idx);
+                for (int64_t t = 0; t < nt && na < c; ++t) add[na++] = tie[t].i;
+                free(tie);
+            }
+            free(cand);
+            ++l;
+            J = grow(J, &capJ, p + na, sizeof(int32_t));
+            m = realloc(m, sizeof(double) * (size_t)capJ);
+            for (int t = 0; t < na; ++t) { J[p + t] = add[t]; NOTE_COLUMN(add[t]); }
+            p += na;
+            qsort(J, (size_t)p, sizeof(int32_t), cmp_i32);
+            SOLVE(1);
+            DROP();
+            s = residual(A, k, J, p, m, w, &rho, &nnzJ);
+            res_flops += 2.0 * nnzJ + 2.0 * (double)s;
+            continue;
+        }
         /* dominant rows among L \ R (Algorithm 1, Eq. 3.2) */
         double rinf = 0.0;
         for (int64_t i = 0; i < s; ++i) if (fabs(w->r[i]) > rinf) rinf = fabs(w->r[i]);
@@ -450,6 +544,7 @@ static void rsai_column(const omat *A, const oparams *P, int64_t k, ocol *out, o
     out->qr_flops = qr_flops;
     out->res_flops = res_flops;
     out->bytes = bytes;
+    out->sel_flops = sel_flops;
     free(Rset);
     free(seen);
     (void)n;
@@ -462,9 +557,9 @@ static void rsai_column(const omat *A, const oparams *P, int64_t k, ocol *out, o
 void *ro_build(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const double *val,
                const int64_t *col_ptr, const int32_t *row_idx, const double *cval,
                int32_t c, int32_t l_max, double eps, int32_t drop_mode, double tol, double tie_band,
-               const int64_t *cols, int64_t ncols, int32_t nthreads, int32_t init_mode) {
+               const int64_t *cols, int64_t ncols, int32_t nthreads, int32_t init_mode, int32_t select_mode) {
     omat A = {n, row_ptr, col_idx, val, col_ptr, row_idx, cval};
-    oparams P = {c, l_max, drop_mode, init_mode, eps, tol, tie_band, ro_norm1(n, col_ptr, cval)};
+    oparams P = {c, l_max, drop_mode, init_mode, eps, tol, tie_band, ro_norm1(n, col_ptr, cval), select_mode};
     oresult *res = calloc(1, sizeof(oresult));
     if (!cols) ncols = n;
     res->ncols = ncols;
@@ -496,7 +591,7 @@ int64_t ro_nnz(const void *h) {
 
 /* Column-wise (CSC-like) export; any output pointer may be NULL. */
 void ro_export(const void *h, int64_t *colptr, int32_t *rows, double *vals, double *rho,
-               int32_t *loops, int32_t *flags, double *counters /* ncols x 8 */) {
+               int32_t *loops, int32_t *flags, double *counters /* ncols x 9 */) {
     const oresult *r = h;
     int64_t off = 0;
     for (int64_t t = 0; t < r->ncols; ++t) {
@@ -511,9 +606,9 @@ void ro_export(const void *h, int64_t *colptr, int32_t *rows, double *vals, doub
         if (loops) loops[t] = c->loops;
         if (flags) flags[t] = c->flags;
         if (counters) {
-            double *o = counters + 8 * t;
+            double *o = counters + 9 * t;
             o[0] = c->qr_flops; o[1] = c->res_flops; o[2] = c->bytes; o[3] = c->solves;
-            o[4] = c->drops; o[5] = c->p_max; o[6] = c->q_max; o[7] = c->p;
+            o[4] = c->drops; o[5] = c->p_max; o[6] = c->q_max; o[7] = c->p; o[8] = c->sel_flops;
         }
     }
     if (colptr) colptr[r->ncols] = off;

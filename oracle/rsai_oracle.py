@@ -48,7 +48,8 @@ def _load():
             lib.ro_build.restype = ctypes.c_void_p
             lib.ro_build.argtypes = mat + [ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                            ctypes.c_int32, ctypes.c_double, ctypes.c_double,
-                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]
+                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32]
             lib.ro_nnz.restype = ctypes.c_int64
             lib.ro_nnz.argtypes = [ctypes.c_void_p]
             lib.ro_export.restype = None
@@ -83,7 +84,7 @@ class OracleM:
     rho: np.ndarray  # ||r_k||
     loops: np.ndarray  # loops l used
     flags: np.ndarray  # FLAG_* bits
-    counters: np.ndarray  # [qr_flops, res_flops, bytes, solves, drops, p_max, q_max, p]
+    counters: np.ndarray  # [qr_flops, res_flops, bytes, solves, drops, p_max, q_max, p, sel_flops]
 
     @property
     def nnz(self) -> int:
@@ -119,10 +120,12 @@ class OracleM:
 
 
 def build(A, c=3, l_max=10, eps=0.3, drop="fixed", tol=1e-3, tie_band=1e-12, cols=None, threads=0,
-          init="identity") -> OracleM:
+          init="identity", select="rsai") -> OracleM:
     """RSAI(tol) columns of M (Algorithm 1 + Eq. 4.3) for the given columns.
     ``init``: the initial pattern J_k^(0) of Algorithm 1, "identity" ({k})
-    or "A" (the rows of column k of A)."""
+    or "A" (the rows of column k of A).  ``select``: "rsai" (dominant rows,
+    Algorithm 1) or "spai" (the c most profitable indices of Section 2,
+    Eqs. 2.5-2.7), the same solve, drop and residual otherwise."""
     lib = _load()
     args = _mat(A)
     mode = _DROP[drop] if isinstance(drop, str) else int(drop)
@@ -133,7 +136,8 @@ def build(A, c=3, l_max=10, eps=0.3, drop="fixed", tol=1e-3, tie_band=1e-12, col
         colsa = np.ascontiguousarray(cols, dtype=np.int64)
         ptr = colsa.ctypes.data_as(ctypes.c_void_p)
     h = lib.ro_build(*args, int(c), int(l_max), float(eps), mode, float(tol), float(tie_band),
-                     ptr, int(len(colsa)), int(threads), {"identity": 0, "A": 1}[init])
+                     ptr, int(len(colsa)), int(threads), {"identity": 0, "A": 1}[init],
+                     {"rsai": 0, "spai": 1}[select])
     try:
         nnz = lib.ro_nnz(h)
         nc = len(colsa)
@@ -143,7 +147,7 @@ def build(A, c=3, l_max=10, eps=0.3, drop="fixed", tol=1e-3, tie_band=1e-12, col
         rho = np.zeros(max(nc, 1))
         loops = np.zeros(max(nc, 1), np.int32)
         flags = np.zeros(max(nc, 1), np.int32)
-        counters = np.zeros((max(nc, 1), 8))
+        counters = np.zeros((max(nc, 1), 9))
         lib.ro_export(h, colptr, rows, vals, rho, loops, flags, counters)
     finally:
         lib.ro_free(h)
