@@ -382,8 +382,11 @@ def main():
     sm_max_mhz = clocks.get("sm_max_mhz") or 2070.0
 
     def roofline(stats, ph, precision):
+        # the warp-bin phase runs bin H (half a warp per column) and then bins W, W2 (a warp per column)
         t = ph["bin_warp"] / 1e3
+        all_in_h = stats.get("cols_bin_half", 0) == stats["n"]
         all_in_w = stats["cols_bin"][0] == stats["n"]
+        kname = "k_bin_half" if all_in_h else "k_bin_warp"
         if precision == "fp32_refine":
             F32 = stats["qr_flops"] + stats["refine_flops"]
             F64 = stats["res_flops"] + stats["refine_flops_f64"]
@@ -395,15 +398,17 @@ def main():
         F, P = (F32, f32_meas) if pipe == "fp32" else (F64, f64_meas)
         P_units = fp32_units_peak(sms, sm_max_mhz) if pipe == "fp32" else PEAK_FP64_PUBLISHED
         return {
-            "bound": "alu", "pipe": pipe, "kernel": f"k_bin_warp<{'float' if precision != 'fp64' else 'double'}>",
+            "bound": "alu", "pipe": pipe, "kernel": f"{kname}<{'float' if precision != 'fp64' else 'double'}>",
             "achieved": F / t / 1e12, "peak": P / 1e12, "unit": "TFLOP/s", "frac": (F / t) / P,
-            "traffic": traffic_from_profiles("k_bin_warp", precision),
+            "traffic": traffic_from_profiles(kname, precision),
             "peak_source": f"measured on this GPU: FMA-chain kernel (rsai_peak_fma), {pipe.upper()}",
             "peak_units": P_units / 1e12, "frac_of_units_peak": (F / t) / P_units,
             "peak_units_source": (f"{sms} SMs x 128 lanes x 2 flop x {sm_max_mhz:.0f} MHz" if pipe == "fp32"
                                   else "published GB300 FP64 rate"),
             "launch_ms": ph["bin_warp"], "flops_fp32": F32, "flops_fp64": F64,
-            "t_roof_ms": 1e3 * max(t32, t64, stats["bytes"] / (hbm_gbs * 1e9)), "all_columns_in_kernel": all_in_w,
+            "t_roof_ms": 1e3 * max(t32, t64, stats["bytes"] / (hbm_gbs * 1e9)),
+            "all_columns_in_kernel": all_in_h or (kname == "k_bin_warp" and all_in_w),
+            "columns_half_bin": stats.get("cols_bin_half", 0),
             "algorithmic_bytes": stats["bytes"], "hbm_gbs": hbm_gbs, "hbm_source": hbm_src, "sms": sms,
         }
 

@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define RSAI_ABI_VERSION 1
+#define RSAI_ABI_VERSION 2
 
 typedef enum {
     RSAI_OK = 0,
@@ -92,9 +92,16 @@ enum {
 enum {
     /* bit 0 is reserved: the input checks (ranges, sortedness, the CSR/CSC
        pairing) always run and report status codes, so there is no flag for them */
-    RSAI_FLAG_INIT_PATTERN_A = 2u /* initial pattern J_k^(0) = rows of column k of A instead of {k}
-                                     (Algorithm 1 leaves it to the user; Section 3 suggests
-                                     that of I, the default, when A has a nonzero diagonal) */
+    RSAI_FLAG_INIT_PATTERN_A = 2u, /* initial pattern J_k^(0) = rows of column k of A instead of {k}
+                                      (Algorithm 1 leaves it to the user; Section 3 suggests
+                                      that of I, the default, when A has a nonzero diagonal) */
+    RSAI_FLAG_SELECT_SPAI = 4u     /* SPAI's choice of new indices (Section 2, Eqs. 2.5-2.7) instead of
+                                      the dominant rows of Algorithm 1: the candidates are the nonzero
+                                      columns of the rows where r_k != 0, less J_k, and the c with the
+                                      smallest rho_j^2 = ||r_k||^2 - (r_k^T A e_j)^2 / ||A e_j||^2 are
+                                      added (ties by lowest index within tie_band * ||r_k||^2); a loop
+                                      with no candidate ends the column.  Solve, drop and residual
+                                      are RSAI(tol)'s.  The method the paper compares with (Section 5.2). */
 };
 
 /* Parameters of RSAI(tol) (Algorithm 1; Section 3 defaults c ~ 3,
@@ -131,6 +138,8 @@ typedef struct {
     int64_t n_rank;       /* columns flagged rank deficient */
     int64_t n_nonfinite;  /* columns with a non-finite value */
     int64_t n_failed;     /* columns no bin could hold (then status WORKSPACE) */
+    int64_t cols_bin_half; /* of cols_bin[0]: columns finished by the half-warp bin (|I| <= 48, |J| <= 16) */
+    double select_flops;  /* RSAI_FLAG_SELECT_SPAI only: FP64 flops of the candidates' rho_j (Eq. 2.7) */
 } rsai_stats;
 
 /* Per-column outcome bits (rsai_get_columns). */
@@ -322,6 +331,9 @@ typedef struct {
     int32_t warp_bin_ctas_per_sm; /* resident CTAs per SM of the warp bin, 0 = as many as fit */
     int32_t small_qr_max_p;       /* largest |J| solved by the register-resident warp QR, 0..16 (16) */
     int32_t global_bin_ctas;      /* CTAs of the global bin, 0 = one per column that reaches it, <= SMs */
+    int32_t half_bin;             /* 1: columns start in the half-warp bin (two columns per warp, |I| <= 48,
+                                     |J| <= 16) and move on to the warp bin when they outgrow it; 0: they start
+                                     in the warp bin.  Default 1 for RSAI_FP64, 0 for RSAI_FP32_REFINE. */
 } rsai_tuning;
 
 /* Read / replace a handle's launch shapes (no counterpart in the paper); the

@@ -1,8 +1,9 @@
 """Autotuner of the size-bin launch shapes (rsai_set_tuning).
 
 For a built handle it times graph-replayed rebuilds under each candidate
-shape (warps per CTA of the warp bin, resident CTAs per SM, the largest |J|
-given to the register-resident warp QR), keeps the fastest and caches it in a
+shape (warps per CTA of the warp bins, the largest |J| given to the
+register-resident QR, and whether columns start in the half-warp bin), keeps
+the fastest and caches it in a
 JSON file keyed by GPU name, precision and a coarse signature of the problem
 (n and nnz/n rounded to powers of two), so later builds of similar problems
 start from the cached shape.  The CTA shapes leave results bit-identical;
@@ -17,8 +18,8 @@ import os
 from . import rsai
 
 DEFAULT_CANDIDATES = [
-    dict(warp_bin_warps=w, warp_bin_ctas_per_sm=0, small_qr_max_p=sp, global_bin_ctas=0)
-    for w in (2, 4, 8) for sp in (0, 8, 16)
+    dict(warp_bin_warps=w, warp_bin_ctas_per_sm=0, small_qr_max_p=sp, global_bin_ctas=0, half_bin=hb)
+    for hb in (0, 1) for w in (2, 4, 8) for sp in (0, 8, 16)
 ]
 
 

@@ -4,6 +4,9 @@
 //
 // Bins (one persistent launch each, columns pulled from an atomic queue; the
 // columns are independent, Section 2 Eq. 2.2):
+//   H  half a warp per column, two columns per warp, workspace in shared
+//      memory (the smallest LS problems: |I| <= 48, |J| <= 16, e.g. 3-D
+//      7-point stencils)
 //   W  one warp per column, workspace in shared memory (small LS problems,
 //      e.g. stencil matrices: |I| <= 64, |J| <= 32)
 //   W2 the same kernel with |I| <= 128 (fewer warps per SM)
@@ -81,6 +84,7 @@ __device__ void emit_or_forward(const Team &team, Column<Team, T> &col, int st, 
         w.ctr[CTR_REFINE] += col.c_ref;
         w.ctr[CTR_REFINE64] += col.c_ref64;
         w.ctr[CTR_BYTES] += col.c_bytes;
+        w.ctr[CTR_SELECT] += col.c_sel;
         w.ctr[CTR_LOOPS] += col.l;
         w.ctr[CTR_SOLVES] += col.c_solves;
         w.ctr[CTR_DROPS] += col.c_drops;
@@ -116,35 +120,49 @@ __device__ void run_queue(const Team &team, Work<T> &w, const DevA &A, const Dev
     for (int i = me; i < CTR_COUNT; i += Team::SIZE) w.ctr[i] = 0;
     team.sync();
     const int64_t nq = Q.count ? (int64_t)(*(volatile const uint32_t *)Q.count) : Q.n;
+    // Half-warp teams: the two halves of a warp start their columns together
+    // (one vote of the whole warp per column), so that similar columns run in
+    // step and each instruction serves both; a half whose queue is empty sits
+    // the round out.  The loop ends only when neither half has a column, so
+    // every lane of the warp reaches each whole-warp vote and synchronisation.
+    constexpr bool paired = std::is_same<Team, HalfTeam>::value;
     for (;;) {
         uint32_t idx = 0;
         if (me == 0) idx = atomicAdd(Q.next, 1u);
         idx = team.bcast(idx, 0);
-        if ((int64_t)idx >= nq) break;
-        int32_t k = Q.cols ? Q.cols[idx] : (int32_t)idx;
-        Column<Team, T> col(team, A, P, cap, w, k);
-        if constexpr (MODE == MODE_BUILD) {
-            int st = col.run();
-            emit_or_forward(team, col, st, Q, O, last_bin, bin);
+        const bool have = (int64_t)idx < nq;
+        if constexpr (paired) {
+            if (!__any_sync(0xffffffffu, have)) break;
         } else {
-            const int64_t mo = F.Mcolptr[k];
-            const int pk = (int)(F.Mcolptr[k + 1] - mo);
-            bool ok = col.load_pattern(F.Mrows + mo, pk);
-            if (ok) {
-                if constexpr (MODE == MODE_REFIT) ok = col.refit();
-                else ok = col.adjoint(F);
-            }
-            if (!ok) {
-                forward_frozen(me, Q, O, k, last_bin, w.ctr);
-            } else {
-                if constexpr (MODE == MODE_REFIT) {
-                    for (int c = me; c < pk; c += Team::SIZE) F.Mval_csr[F.Mcsc_to_csr[mo + c]] = w.m[c];
-                    if (me == 0) F.rho2[k] = col.rho * col.rho;
-                }
-                if (me == 0) w.ctr[CTR_COLS] += 1;
-            }
-            team.sync();
+            if (!have) break;
         }
+        if (have) {
+            const int32_t k = Q.cols ? Q.cols[idx] : (int32_t)idx;
+            Column<Team, T> col(team, A, P, cap, w, k);
+            if constexpr (MODE == MODE_BUILD) {
+                int st = col.run();
+                emit_or_forward(team, col, st, Q, O, last_bin, bin);
+            } else {
+                const int64_t mo = F.Mcolptr[k];
+                const int pk = (int)(F.Mcolptr[k + 1] - mo);
+                bool ok = col.load_pattern(F.Mrows + mo, pk);
+                if (ok) {
+                    if constexpr (MODE == MODE_REFIT) ok = col.refit();
+                    else ok = col.adjoint(F);
+                }
+                if (!ok) {
+                    forward_frozen(me, Q, O, k, last_bin, w.ctr);
+                } else {
+                    if constexpr (MODE == MODE_REFIT) {
+                        for (int c = me; c < pk; c += Team::SIZE) F.Mval_csr[F.Mcsc_to_csr[mo + c]] = w.m[c];
+                        if (me == 0) F.rho2[k] = col.rho * col.rho;
+                    }
+                    if (me == 0) w.ctr[CTR_COLS] += 1;
+                }
+                team.sync();
+            }
+        }
+        if constexpr (paired) __syncwarp();
     }
     team.sync();
     if (me == 0) {
@@ -167,6 +185,18 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 8 ? 1 : 2))
     w.carve(smem + (size_t)wid * Work<T>::bytes(cap), cap);
     WarpTeam team;
     run_queue<MODE>(team, w, A, P, cap, Q, O, F, gctr, last_bin != 0, 0);
+}
+
+// Bin H: every half warp is a team with its own workspace and its own column
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256, (sizeof(T) == 8 ? 1 : 2))
+    k_bin_half(DevA A, DevParams P, Caps cap, ColQueue Q, ColOut O, Frozen F, unsigned long long *gctr, int last_bin) {
+    extern __shared__ __align__(16) char smem[];
+    const int tid = threadIdx.x >> 4;
+    Work<T> w;
+    w.carve(smem + (size_t)tid * Work<T>::bytes(cap), cap);
+    HalfTeam team;
+    run_queue<MODE>(team, w, A, P, cap, Q, O, F, gctr, last_bin != 0, kBinHalf);
 }
 
 template <typename T, int NT, int MODE>
@@ -192,6 +222,9 @@ __global__ void __launch_bounds__(NT, 1)
 
 template <typename T>
 size_t warp_bin_smem(const Caps &c, int warps) { return (size_t)warps * Work<T>::bytes(c); }
+
+template <typename T>
+size_t half_bin_smem(const Caps &c, int warps) { return (size_t)(2 * warps) * Work<T>::bytes(c); }
 
 template <typename T>
 size_t work_bytes(const Caps &c) { return Work<T>::bytes(c); }
@@ -223,6 +256,16 @@ static cudaError_t launch_warp_t(int grid, int warps, const DevA &A, const DevPa
 }
 
 template <typename T, int MODE>
+static cudaError_t launch_half_t(int grid, int warps, const DevA &A, const DevParams &P, const Caps &cap,
+                                 const ColQueue &Q, const ColOut &O, const Frozen &F, unsigned long long *gctr,
+                                 bool last, cudaStream_t st) {
+    size_t smem = half_bin_smem<T>(cap, warps);
+    allow_full_smem(k_bin_half<T, MODE>);
+    k_bin_half<T, MODE><<<grid, warps * 32, smem, st>>>(A, P, cap, Q, O, F, gctr, last ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <typename T, int MODE>
 static cudaError_t launch_block_t(int grid, const DevA &A, const DevParams &P, const Caps &cap, const ColQueue &Q,
                                   const ColOut &O, const Frozen &F, unsigned long long *gctr, bool last, char *gwork,
                                   size_t gstride, int bin, cudaStream_t st) {
@@ -244,6 +287,19 @@ cudaError_t launch_bin_warp(int mode, bool fp32, int grid, int warps, const DevA
     if (mode == MODE_BUILD) return launch_warp_t<double, MODE_BUILD>(grid, warps, A, P, cap, Q, O, F, gctr, last, st);
     if (mode == MODE_REFIT) return launch_warp_t<double, MODE_REFIT>(grid, warps, A, P, cap, Q, O, F, gctr, last, st);
     return launch_warp_t<double, MODE_BACKWARD>(grid, warps, A, P, cap, Q, O, F, gctr, last, st);
+}
+
+cudaError_t launch_bin_half(int mode, bool fp32, int grid, int warps, const DevA &A, const DevParams &P,
+                            const Caps &cap, const ColQueue &Q, const ColOut &O, const Frozen &F,
+                            unsigned long long *gctr, bool last, cudaStream_t st) {
+    if (fp32) {
+        if (mode == MODE_BUILD) return launch_half_t<float, MODE_BUILD>(grid, warps, A, P, cap, Q, O, F, gctr, last, st);
+        if (mode == MODE_REFIT) return launch_half_t<float, MODE_REFIT>(grid, warps, A, P, cap, Q, O, F, gctr, last, st);
+        return launch_half_t<float, MODE_BACKWARD>(grid, warps, A, P, cap, Q, O, F, gctr, last, st);
+    }
+    if (mode == MODE_BUILD) return launch_half_t<double, MODE_BUILD>(grid, warps, A, P, cap, Q, O, F, gctr, last, st);
+    if (mode == MODE_REFIT) return launch_half_t<double, MODE_REFIT>(grid, warps, A, P, cap, Q, O, F, gctr, last, st);
+    return launch_half_t<double, MODE_BACKWARD>(grid, warps, A, P, cap, Q, O, F, gctr, last, st);
 }
 
 cudaError_t launch_bin_block(int mode, bool fp32, int grid, const DevA &A, const DevParams &P, const Caps &cap,
@@ -271,6 +327,19 @@ int occupancy_bin_warp(bool fp32, int warps, const Caps &cap) {
     } else {
         allow_full_smem(k_bin_warp<double, MODE_BUILD>);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bin_warp<double, MODE_BUILD>, warps * 32, smem);
+    }
+    return nb;
+}
+
+int occupancy_bin_half(bool fp32, int warps, const Caps &cap) {
+    int nb = 0;
+    size_t smem = fp32 ? half_bin_smem<float>(cap, warps) : half_bin_smem<double>(cap, warps);
+    if (fp32) {
+        allow_full_smem(k_bin_half<float, MODE_BUILD>);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bin_half<float, MODE_BUILD>, warps * 32, smem);
+    } else {
+        allow_full_smem(k_bin_half<double, MODE_BUILD>);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bin_half<double, MODE_BUILD>, warps * 32, smem);
     }
     return nb;
 }

@@ -40,6 +40,7 @@ struct Caps {
     int stage_bytes;  // shared memory for staging QR panels (global-memory bins), 0 = none
     int append;       // CTA bins: keep the factor between loops and append to it (Section 3)
     int dcap;         // max number of distinct columns dropped from J (they are not charged again on re-entry)
+    int spai;         // SPAI selection: a score per candidate column (scap of them)
 };
 
 template <typename T> struct Work {
@@ -48,6 +49,7 @@ template <typename T> struct Work {
     long long *ctr;
     int32_t *I, *S, *J, *Jn, *Rset, *buf, *buf2, *Rhat, *hkey, *hval;
     int32_t *D;        // columns dropped from J so far, ascending
+    double *sc;        // SPAI: the score s_j of each candidate (Caps::spai)
     int32_t *Ip, *Jp;  // factor position of each sorted I / J entry (Caps::append)
     T *qte;            // Q^T e_k(I) of the kept factor, factor row order (Caps::append)
     char *stage = nullptr;  // panel staging area (shared memory), not part of the carved workspace
@@ -71,6 +73,7 @@ template <typename T> struct Work {
         b += align16(sizeof(int32_t) * 32);
         b += 2 * align16(sizeof(int32_t) * (size_t)c.hcap);
         b += align16(sizeof(int32_t) * (size_t)c.dcap);
+        if (c.spai) b += align16(sizeof(double) * (size_t)c.scap);
         if (c.append) {
             b += align16(sizeof(int32_t) * (size_t)c.qcap);
             b += align16(sizeof(int32_t) * (size_t)c.pcap);
@@ -100,6 +103,10 @@ template <typename T> struct Work {
         hkey = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.hcap);
         hval = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.hcap);
         D = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.dcap);
+        sc = nullptr;
+        if (c.spai) {
+            sc = (double *)(base + o); o += align16(sizeof(double) * (size_t)c.scap);
+        }
         Ip = Jp = nullptr;
         qte = nullptr;
         if (c.append) {
@@ -115,15 +122,22 @@ enum ColStatus { COL_DONE = 0, COL_OVERFLOW = 1 };
 // Entries of a CSR row loaded together in the row-driven loops
 constexpr int kRowGroup = 4;
 
-// Sort buf[0..len) ascending: registers and shuffles on a warp (up to 256
-// elements), bitonic in shared memory otherwise.
+// Rows per lane of the register QR: q <= 64 on a warp, q <= 48 on half a warp
+template <class Team> constexpr int kRegRows = Team::SIZE == 16 ? 3 : 2;
+
+// Sort buf[0..len) ascending: registers and shuffles on a warp or half warp
+// (up to 256 elements), bitonic in shared memory otherwise.
 template <class Team>
 __device__ void team_sort_i32(const Team &team, int32_t *buf, int len) {
-    if constexpr (std::is_same<Team, WarpTeam>::value) {
-        if (len <= 32) { warp_sort_regs<1>(buf, len); return; }
-        if (len <= 64) { warp_sort_regs<2>(buf, len); return; }
-        if (len <= 128) { warp_sort_regs<4>(buf, len); return; }
-        if (len <= 256) { warp_sort_regs<8>(buf, len); return; }
+    if constexpr (is_lane_team<Team>::value) {
+        constexpr int W = Team::SIZE;
+        if (len <= W) { lanes_sort_regs<W, 1>(buf, len); return; }
+        if (len <= 2 * W) { lanes_sort_regs<W, 2>(buf, len); return; }
+        if (len <= 4 * W) { lanes_sort_regs<W, 4>(buf, len); return; }
+        if (len <= 8 * W) { lanes_sort_regs<W, 8>(buf, len); return; }
+        if constexpr (W == 16) {
+            if (len <= 16 * W) { lanes_sort_regs<W, 16>(buf, len); return; }
+        }
     }
     team_sort_i32_smem(team, buf, len);
 }
@@ -177,8 +191,9 @@ template <class Team, typename T>
 __device__ __forceinline__ void householder_step(const Team &team, T *B, int q, int p, T *rhs, T *vhead, T *taus,
                                                  int j, int c_begin, T small, int &rank_flag) {
     const int me = team.rank();
-    const int lane = me & 31, wid = me >> 5;
-    constexpr int NW = (Team::SIZE + 31) / 32;
+    constexpr int LN = Team::LANES;  // lanes of one group: the team itself, or one warp of a CTA
+    constexpr int NW = Team::SIZE / LN;
+    const int lane = me % LN, wid = me / LN;
     T *col = B + (int64_t)j * q;
     T part = 0;
     for (int i = j + me; i < q; i += Team::SIZE) part += col[i] * col[i];
@@ -193,11 +208,10 @@ __device__ __forceinline__ void householder_step(const Team &team, T *B, int q, 
         for (int c = c_begin + wid; c <= p; c += NW) {
             T *t = (c < p) ? B + (int64_t)c * q : rhs;
             T d = 0;
-            for (int i = j + lane; i < q; i += 32) d += ((i == j) ? v0 : col[i]) * t[i];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            for (int i = j + lane; i < q; i += LN) d += ((i == j) ? v0 : col[i]) * t[i];
+            d = team.lanes_sum(d);
             const T f = d * two_over;
-            for (int i = j + lane; i < q; i += 32) t[i] -= f * ((i == j) ? v0 : col[i]);
+            for (int i = j + lane; i < q; i += LN) t[i] -= f * ((i == j) ? v0 : col[i]);
         }
     }
     team.sync();
@@ -552,6 +566,171 @@ __device__ __noinline__ int pattern_of_column(Team team, const int64_t *col_ptr,
     return len;
 }
 
+// J -> position in J: an open-addressing hash of J (hcap slots, warp bins)
+// or a binary search of the sorted J (hcap = 0).
+struct JSet {
+    const int32_t *J, *hkey, *hval;
+    int p, hcap;
+    __device__ __forceinline__ unsigned slot(int32_t col) const {
+        return ((unsigned)col * 0x9E3779B1u) >> (32 - __ffs(hcap) + 1);
+    }
+    __device__ __forceinline__ int find(int32_t col) const {
+        if (hcap == 0) return find_i32(J, p, col);
+        const unsigned mask = (unsigned)hcap - 1;
+        unsigned sl = slot(col);
+        for (;;) {
+            const int32_t key = hkey[sl];
+            if (key == col) return hval[sl];
+            if (key == -1) return -1;
+            sl = (sl + 1) & mask;
+        }
+    }
+};
+
+struct SpaiPick {
+    int na;               // columns chosen (in buf, ascending); 0: no candidate; -1: overflow
+    long long bytes, sel; // algorithmic bytes and selection flops
+};
+
+// SPAI's most profitable indices (Section 2, Eqs. 2.5-2.7).  L = rows of S
+// with |r_i| > band (the same reading of r_i != 0 as the dominant rows);
+// the candidates Jhat = cols(A(L,:)) \ J, each scored by one rank walking
+// its CSC column: s_j = (r^T A e_j)^2 / ||A e_j||^2 in double (rho_j^2 =
+// ||r||^2 - s_j, so the largest s_j are the smallest rho_j); the c best by
+// (s_j desc, j asc) with a tie band of tie_band * ||r||^2, the scores
+// compared as ordered integer keys (non-negative doubles).  The chosen
+// columns go to buf in ascending order.  Returns their number, 0 when no
+// candidate is left, -1 on overflow.
+template <class Team>
+__device__ __noinline__ SpaiPick spai_select(Team team, DevA A, int c, double tie_band, int scap, const int32_t *S,
+                                             const double *r, int s, JSet Jset, int32_t *buf, int32_t *buf2,
+                                             double *sc, int32_t *Rhat) {
+    const int me = team.rank();
+    SpaiPick out{0, 0, 0};
+    long long rinf = 0;
+    double rr = 0.0;
+    for (int i = me; i < s; i += Team::SIZE) {
+        rinf = max(rinf, abskey(r[i]));
+        rr = fma(r[i], r[i], rr);
+    }
+    rinf = team.maxv(rinf);
+    rr = team.sum(rr);
+    const long long bk = abskey(tie_band * key_value(rinf));
+    // column indices of the rows of L
+    int tot = 0;
+    long long byt = 0;
+    for (int i0 = 0; i0 < s; i0 += Team::SIZE) {
+        const int i = i0 + me;
+        int len = 0;
+        int64_t st = 0;
+        if (i < s && abskey(r[i]) > bk) {
+            const int32_t row = S[i];
+            st = A.row_ptr[row];
+            len = (int)(A.row_ptr[row + 1] - st);
+            byt += 4LL * len + 16;
+        }
+        int part;
+        const int off = tot + team.scan(len, &part);
+        if (next_pow2(tot + part) > scap) {
+            out.na = -1;
+            return out;
+        }
+        for (int e = 0; e < len; ++e) buf[off + e] = A.col_idx[st + e];
+        tot += part;
+    }
+    out.bytes += team.sum(byt);
+    team.sync();
+    if (tot == 0) return out;
+    team_sort_i32(team, buf, tot);
+    const int nu = team_unique_i32(team, buf, tot, buf2);
+    int nc = 0;
+    for (int i0 = 0; i0 < nu; i0 += Team::SIZE) {
+        const int i = i0 + me;
+        const int f = (i < nu) && (Jset.find(buf2[i]) < 0);
+        int part;
+        const int pos = team.scan(f, &part);
+        if (f) buf[nc + pos] = buf2[i];
+        nc += part;
+    }
+    team.sync();
+    if (nc == 0) return out;
+    // scores (Eq. 2.7)
+    long long sf = 0;
+    byt = 0;
+    for (int t = me; t < nc; t += Team::SIZE) {
+        const int32_t j = buf[t];
+        double dot = 0.0, nrm = 0.0;
+        const int64_t e0 = A.col_ptr[j], e1 = A.col_ptr[j + 1];
+        for (int64_t e = e0; e < e1; ++e) {
+            const double a = A.cval[e];
+            const int pos = find_i32(S, s, A.row_idx[e]);
+            if (pos >= 0) dot = fma(r[pos], a, dot);
+            nrm = fma(a, a, nrm);
+        }
+        sc[t] = (nrm > 0.0) ? dot * dot / nrm : 0.0;
+        sf += 4 * (e1 - e0) + 3;
+        byt += 12 * (e1 - e0) + 16;
+    }
+    out.sel += team.sum(sf);
+    out.bytes += team.sum(byt);
+    team.sync();
+    const bool take_all = nc <= c;
+    long long hik = 0, lob = 0;
+    if (!take_all) {
+        // the c-th score of the (s_j desc, j asc) order: c rounds of argmax
+        long long pa = LLONG_MAX;
+        int pi = -1;
+        for (int t = 0; t < c; ++t) {
+            long long ba = -1;
+            int bi = INT32_MAX;
+            for (int u = me; u < nc; u += Team::SIZE) {
+                const long long a = abskey(sc[u]);
+                const int32_t j = buf[u];
+                if (dom_before(pa, pi, a, j) && dom_before(a, j, ba, bi)) {
+                    ba = a;
+                    bi = j;
+                }
+            }
+            team.argmax(ba, bi);
+            pa = ba;
+            pi = bi;
+        }
+        const double v = key_value(pa), sband = tie_band * rr;
+        hik = abskey(v + sband);
+        lob = __double_as_longlong(v - sband);  // negative bit pattern if v - sband < 0
+    }
+    int nabove = 0;
+    if (!take_all) {
+        for (int u = me; u < nc; u += Team::SIZE) nabove += abskey(sc[u]) > hik;
+        nabove = team.sum(nabove);
+    }
+    const int need = c - nabove;
+    int na = 0, tb = 0;
+    for (int u0 = 0; u0 < nc; u0 += Team::SIZE) {
+        const int u = u0 + me;
+        int above = 0, tie = 0;
+        if (u < nc && !take_all) {
+            const long long a = abskey(sc[u]);
+            above = a > hik;
+            tie = (a >= lob) && (a <= hik);
+        }
+        int tpart;
+        const int trank = team.scan(tie, &tpart);
+        const int sel = (u < nc) && (take_all || above || (tie && tb + trank < need));
+        int part;
+        const int pos = team.scan(sel, &part);
+        if (sel) Rhat[na + pos] = buf[u];
+        na += part;
+        tb += tpart;
+    }
+    team.sync();
+    for (int t = me; t < na; t += Team::SIZE) buf[t] = Rhat[t];
+    team.sync();
+    out.na = na;
+    return out;
+}
+
+
 template <class Team, typename T> struct Column {
     const Team &team;
     const DevA &A;
@@ -567,7 +746,7 @@ template <class Team, typename T> struct Column {
     T fro2_f;      // ||B||_F^2 of the kept factor (Caps::append)
     bool fact_valid;  // B, vhead, tau, qte, Ip, Jp hold the factor of the current J (Caps::append)
     // per-column work counters (integers; committed only when the column finishes)
-    long long c_qr, c_res, c_ref, c_ref64, c_bytes;
+    long long c_qr, c_res, c_ref, c_ref64, c_bytes, c_sel;
     int c_solves, c_drops, c_pmax, c_qmax;
 
     __device__ Column(const Team &t, const DevA &a, const DevParams &pp, const Caps &c, Work<T> &ww, int32_t kk)
@@ -575,17 +754,16 @@ template <class Team, typename T> struct Column {
 
     // J -> position in J: open-addressing hash (warp bins) or binary search.
     // The table's layout may depend on insertion order; lookups do not.
-    __device__ __forceinline__ unsigned hslot(int32_t col) const {
-        return ((unsigned)col * 0x9E3779B1u) >> (32 - __ffs(cap.hcap) + 1);
-    }
+    __device__ __forceinline__ JSet jset() const { return JSet{w.J, w.hkey, w.hval, p, cap.hcap}; }
     __device__ void build_jhash() {
         if (cap.hcap == 0) return;
         for (int i = team.rank(); i < cap.hcap; i += Team::SIZE) w.hkey[i] = -1;
         team.sync();
         const unsigned mask = (unsigned)cap.hcap - 1;
+        const JSet js = jset();
         for (int c = team.rank(); c < p; c += Team::SIZE) {
             const int32_t key = w.J[c];
-            unsigned sl = hslot(key);
+            unsigned sl = js.slot(key);
             for (;;) {
                 int32_t old = atomicCAS(&w.hkey[sl], -1, key);
                 if (old == -1) { w.hval[sl] = c; break; }
@@ -594,17 +772,7 @@ template <class Team, typename T> struct Column {
         }
         team.sync();
     }
-    __device__ __forceinline__ int find_J(int32_t col) const {
-        if (cap.hcap == 0) return find_i32(w.J, p, col);
-        const unsigned mask = (unsigned)cap.hcap - 1;
-        unsigned sl = hslot(col);
-        for (;;) {
-            int32_t key = w.hkey[sl];
-            if (key == col) return w.hval[sl];
-            if (key == -1) return -1;
-            sl = (sl + 1) & mask;
-        }
-    }
+    __device__ __forceinline__ int find_J(int32_t col) const { return jset().find(col); }
 
     // I = sorted rows of A(:,J) (Section 2).  Returns false on overflow.
     __device__ bool rows_of_J() {
@@ -643,13 +811,13 @@ template <class Team, typename T> struct Column {
     // Householder QR of B (q x p, ld q) applied to rhs, then back substitution
     // into rhs[0..p); the reflectors stay in B (tails), vhead and tau.
     __device__ void qr_solve(T small) {
-        if constexpr (std::is_same<Team, WarpTeam>::value) {
-            if (p > 2 && p <= cap.small_p && q <= kSmallQ) {
-                rank_flag = warp_qr_small(w.B, q, p, w.rhs, w.vhead, w.tau, small);
+        if constexpr (is_lane_team<Team>::value) {
+            if (p > 2 && p <= cap.small_p && q <= Team::SIZE * kRegRows<Team>) {
+                rank_flag = lanes_qr_small<Team::SIZE, kRegRows<Team>>(w.B, q, p, w.rhs, w.vhead, w.tau, small);
                 return;
             }
         }
-        if constexpr (!std::is_same<Team, WarpTeam>::value) {
+        if constexpr (!is_lane_team<Team>::value) {
             const bool keep = cap.append != 0;  // keep Q^T e_k for later updates
             if (cap.stage_bytes > 0 && p >= 2 * kPanel)
                 rank_flag = qr_solve_staged<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.tau, small, (T *)w.stage,
@@ -676,19 +844,19 @@ template <class Team, typename T> struct Column {
 
     // factor row of sorted I position i / factor column of sorted J position c
     __device__ __forceinline__ int frow(int i) const {
-        if constexpr (std::is_same<Team, WarpTeam>::value) return i;
+        if constexpr (is_lane_team<Team>::value) return i;
         else return cap.append ? w.Ip[i] : i;
     }
     __device__ __forceinline__ int fcol(int c) const {
-        if constexpr (std::is_same<Team, WarpTeam>::value) return c;
+        if constexpr (is_lane_team<Team>::value) return c;
         else return cap.append ? w.Jp[c] : c;
     }
 
     // rhs <- R^{-1} Q^T rhs with the stored reflectors
     __device__ void apply_qt_solve(T small) {
-        if constexpr (std::is_same<Team, WarpTeam>::value) {
-            if (p > 2 && p <= cap.small_p && q <= kSmallQ) {
-                warp_apply_qt_small(w.B, q, p, w.rhs, w.vhead, w.tau, small);
+        if constexpr (is_lane_team<Team>::value) {
+            if (p > 2 && p <= cap.small_p && q <= Team::SIZE * kRegRows<Team>) {
+                lanes_apply_qt_small<Team::SIZE, kRegRows<Team>>(w.B, q, p, w.rhs, w.vhead, w.tau, small);
                 return;
             }
         }
@@ -774,7 +942,7 @@ template <class Team, typename T> struct Column {
     // of refactoring when the last solve left one.
     __device__ bool solve(bool append) {
         const int me = team.rank();
-        if constexpr (!std::is_same<Team, WarpTeam>::value) {
+        if constexpr (!is_lane_team<Team>::value) {
             if (cap.append && append && fact_valid) {
                 const int st = update_factor();
                 if (st == 0) return false;
@@ -820,7 +988,7 @@ template <class Team, typename T> struct Column {
             }
         }
         const T fro2s = team.sum(fro2);
-        if constexpr (!std::is_same<Team, WarpTeam>::value) fro2_f = fro2s;
+        if constexpr (!is_lane_team<Team>::value) fro2_f = fro2s;
         T fro = sqrt(fro2s);
         team.sync();
         const T small = T(q) * T(2.0 * Unit<T>::u) * fro;
@@ -1124,25 +1292,32 @@ template <class Team, typename T> struct Column {
         return true;
     }
 
-    // Jhat = cols(A(Rhat,:)) \ J into w.buf; returns |Jhat| or -1 on overflow
+    // Jhat = cols(A(Rhat,:)) \ J into w.buf; returns |Jhat| or -1 on overflow.
+    // The rows of Rhat are dealt out to the team's ranks, as many passes as
+    // |Rhat| (<= c <= 32) needs on a team of 16.
     __device__ int new_columns(int nh) {
         const int me = team.rank();
-        int len = 0;
-        int64_t st = 0;
-        if (me < nh) {
-            st = A.row_ptr[w.Rhat[me]];
-            len = (int)(A.row_ptr[w.Rhat[me] + 1] - st);
-        }
-        int tot;
-        int off = team.scan(len, &tot);
-        if (next_pow2(tot) > cap.scap) return -1;
-        for (int e = 0; e < len; e += 4) {
-            int32_t v[4];
+        int tot = 0;
+        for (int t0 = 0; t0 < nh; t0 += Team::SIZE) {
+            const int t = t0 + me;
+            int len = 0;
+            int64_t st = 0;
+            if (t < nh) {
+                st = A.row_ptr[w.Rhat[t]];
+                len = (int)(A.row_ptr[w.Rhat[t] + 1] - st);
+            }
+            int part;
+            const int off = tot + team.scan(len, &part);
+            if (next_pow2(tot + part) > cap.scap) return -1;
+            for (int e = 0; e < len; e += 4) {
+                int32_t v[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = (e + u < len) ? A.col_idx[st + e + u] : 0;
+                for (int u = 0; u < 4; ++u) v[u] = (e + u < len) ? A.col_idx[st + e + u] : 0;
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (e + u < len) w.buf[off + e + u] = v[u];
+                for (int u = 0; u < 4; ++u)
+                    if (e + u < len) w.buf[off + e + u] = v[u];
+            }
+            tot += part;
         }
         team.sync();
         team_sort_i32(team, w.buf, tot);
@@ -1190,8 +1365,8 @@ template <class Team, typename T> struct Column {
     // J = Jk (sorted, length pk): false if it does not fit this bin
     __device__ bool load_pattern(const int32_t *Jk, int pk) {
         p = pk; q = 0; s = 0; nR = 0; l = 0; nD = 0; q0 = 0; p0 = 0; rank_flag = 0; rho = 0.0;
-        if constexpr (!std::is_same<Team, WarpTeam>::value) fact_valid = false;
-        c_qr = c_res = c_ref = c_ref64 = c_bytes = 0;
+        if constexpr (!is_lane_team<Team>::value) fact_valid = false;
+        c_qr = c_res = c_ref = c_ref64 = c_bytes = c_sel = 0;
         c_solves = c_drops = c_pmax = c_qmax = 0;
         if (pk > cap.pcap || pk < 1) return false;
         for (int c = team.rank(); c < pk; c += Team::SIZE) w.J[c] = Jk[c];
@@ -1336,8 +1511,8 @@ template <class Team, typename T> struct Column {
     __device__ int run() {
         const int me = team.rank();
         p = 1; q = 0; s = 0; nR = 0; l = 0; nD = 0; q0 = 0; p0 = 0; rank_flag = 0; rho = 0.0;
-        if constexpr (!std::is_same<Team, WarpTeam>::value) fact_valid = false;
-        c_qr = c_res = c_ref = c_ref64 = c_bytes = 0;
+        if constexpr (!is_lane_team<Team>::value) fact_valid = false;
+        c_qr = c_res = c_ref = c_ref64 = c_bytes = c_sel = 0;
         c_solves = c_drops = c_pmax = c_qmax = 0;
         if (me == 0) w.J[0] = k;
         team.sync();
@@ -1375,12 +1550,26 @@ template <class Team, typename T> struct Column {
             residual();
             bool grown = false;
             while (!grown && rho > P.eps && l < P.l_max) {
+                if (P.spai) {
+                    const SpaiPick pk = spai_select(team, A, P.c, P.tie_band, cap.scap, w.S, w.r, s, jset(), w.buf,
+                                                    w.buf2, w.sc, w.Rhat);
+                    c_bytes += pk.bytes;
+                    c_sel += pk.sel;
+                    const int na = pk.na;
+                    if (na < 0) return COL_OVERFLOW;
+                    if (na == 0) break;  // no candidate: nothing can be added later either
+                    ++l;
+                    note_bytes_columns(0, na, w.buf);
+                    if (!merge_J(na)) return COL_OVERFLOW;
+                    grown = true;
+                    continue;
+                }
                 int nh = dominant_rows();
                 if (nh == 0) break;
                 if (!add_to_R(nh)) return COL_OVERFLOW;
                 {
                     long long b = 0;
-                    if (me < nh) b = 4 * (A.row_ptr[w.Rhat[me] + 1] - A.row_ptr[w.Rhat[me]]) + 16;
+                    for (int t = me; t < nh; t += Team::SIZE) b += 4 * (A.row_ptr[w.Rhat[t] + 1] - A.row_ptr[w.Rhat[t]]) + 16;
                     c_bytes += team.sum(b);
                 }
                 int nj = new_columns(nh);

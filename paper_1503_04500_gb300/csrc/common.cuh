@@ -1,10 +1,12 @@
 // common.cuh -- device-side building blocks shared by the RSAI kernels.
 //
 // A "team" is the group of threads that works on one column of M at a time:
-// a warp (WarpTeam) for small least-squares problems, a whole CTA (BlockTeam)
-// for larger ones.  The column algorithm (column.cuh) is written once against
-// this interface: rank()/size, sync(), sums, maxima, argmax with a
-// (value desc, index asc) order, exclusive scans and a bitonic sort.
+// half a warp (HalfTeam, two columns per warp) or a warp (WarpTeam) for small
+// least-squares problems, a whole CTA (BlockTeam) for larger ones.  The column
+// algorithm (column.cuh) is written once against this interface: rank()/size,
+// sync(), sums, maxima, argmax with a (value desc, index asc) order, exclusive
+// scans and a bitonic sort.  lanes_sum() reduces over the team's lanes within
+// one warp (the whole team unless it spans several warps).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -31,6 +33,7 @@ struct DevA {
 struct DevParams {
     int c, l_max, drop_mode, precision;
     int init_a;  // initial pattern J_k^(0) of Algorithm 1: 0 = {k}, 1 = rows of A(:,k)
+    int spai;    // 1: SPAI's most profitable indices (Eqs. 2.5-2.7) instead of the dominant rows
     double eps, tol, tie_band;
     const double *norm1;       // ||A||_1 per block (one block unless a batch)
     const double *tau_fixed;   // tol / ||A||_1 per block
@@ -40,7 +43,7 @@ struct DevParams {
 // Work counters of one team, summed into the global statistics at the end.
 enum Counter {
     CTR_QR = 0, CTR_RES, CTR_REFINE, CTR_REFINE64, CTR_BYTES, CTR_LOOPS, CTR_SOLVES, CTR_DROPS,
-    CTR_PMAX, CTR_QMAX, CTR_COLS, CTR_RANK, CTR_NONFINITE, CTR_NC, CTR_FROB2, CTR_FAILED,
+    CTR_PMAX, CTR_QMAX, CTR_COLS, CTR_RANK, CTR_NONFINITE, CTR_NC, CTR_FROB2, CTR_FAILED, CTR_SELECT,
     CTR_COUNT
 };
 
@@ -122,8 +125,59 @@ __device__ __forceinline__ bool dom_before(long long a, int i, long long b, int 
 }
 
 // ----------------------------------------------------------------------------
+// Half a warp: lanes 0-15 or 16-31 of a warp work on one column; the two
+// halves of a warp run their columns side by side.  Every shuffle and
+// synchronisation names only the half's own lanes, so the two halves may
+// take different paths through the column algorithm.
+struct HalfTeam {
+    static constexpr int SIZE = 16;
+    static constexpr int LANES = 16;
+    unsigned mask;  // this half's lanes
+    __device__ __forceinline__ HalfTeam() : mask(0xffffu << (threadIdx.x & 16)) {}
+    __device__ __forceinline__ int rank() const { return threadIdx.x & 15; }
+    __device__ __forceinline__ void sync() const { __syncwarp(mask); }
+    template <typename V> __device__ __forceinline__ V sum(V x) const {
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) x += __shfl_xor_sync(mask, x, o);
+        return x;
+    }
+    template <typename V> __device__ __forceinline__ V lanes_sum(V x) const { return sum(x); }
+    template <typename V> __device__ __forceinline__ V maxv(V x) const {
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+            V y = __shfl_xor_sync(mask, x, o);
+            x = y > x ? y : x;
+        }
+        return x;
+    }
+    __device__ __forceinline__ void argmax(long long &a, int &i) const {
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+            long long b = __shfl_xor_sync(mask, a, o);
+            int j = __shfl_xor_sync(mask, i, o);
+            if (dom_before(b, j, a, i)) { a = b; i = j; }
+        }
+    }
+    __device__ __forceinline__ int scan(int x, int *total) const {
+        const int lane = rank();
+        int inc = x;
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) {
+            int y = __shfl_up_sync(mask, inc, o, 16);
+            if (lane >= o) inc += y;
+        }
+        *total = __shfl_sync(mask, inc, 15, 16);
+        return inc - x;
+    }
+    template <typename V> __device__ __forceinline__ V bcast(V x, int src) const {
+        return __shfl_sync(mask, x, src, 16);
+    }
+};
+
 struct WarpTeam {
     static constexpr int SIZE = 32;
+    static constexpr int LANES = 32;
+    static constexpr unsigned mask = 0xffffffffu;
     __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
     __device__ __forceinline__ void sync() const { __syncwarp(); }
     template <typename V> __device__ __forceinline__ V sum(V x) const {
@@ -131,6 +185,7 @@ struct WarpTeam {
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         return x;
     }
+    template <typename V> __device__ __forceinline__ V lanes_sum(V x) const { return sum(x); }
     template <typename V> __device__ __forceinline__ V maxv(V x) const {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -169,11 +224,18 @@ struct WarpTeam {
 // each, holding any reduced type), `redi` as many ints.
 template <int NT> struct BlockTeam {
     static constexpr int SIZE = NT;
+    static constexpr int LANES = 32;
     static constexpr int NW = NT / 32;
     unsigned long long *red;
     int *redi;
     __device__ __forceinline__ int rank() const { return threadIdx.x; }
     __device__ __forceinline__ void sync() const { __syncthreads(); }
+    // sum over the 32 lanes of the calling warp only
+    template <typename V> __device__ __forceinline__ V lanes_sum(V x) const {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        return x;
+    }
     template <typename V> __device__ __forceinline__ V &slot(int w) const { return *reinterpret_cast<V *>(&red[w]); }
     template <typename V> __device__ __forceinline__ V sum(V x) const {
 #pragma unroll
@@ -244,6 +306,12 @@ template <int NT> struct BlockTeam {
         return slot<V>(NW);
     }
 };
+
+// Teams that fit in one warp (one column per warp or half-warp): register QR
+// and register sorts, no kept factor between loops.
+template <class Team> struct is_lane_team { static constexpr bool value = false; };
+template <> struct is_lane_team<WarpTeam> { static constexpr bool value = true; };
+template <> struct is_lane_team<HalfTeam> { static constexpr bool value = true; };
 
 // Bitonic sort of buf[0..len) ascending in shared memory; buf must have room
 // for the next power of two (padded with INT32_MAX).

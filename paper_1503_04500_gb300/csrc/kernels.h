@@ -8,6 +8,11 @@ namespace rsai {
 constexpr int kBlockThreads = 256;  // CTA team size of bins C and G
 constexpr int kWarpsPerCta = 4;     // warps per CTA in bin W
 constexpr int kStatBlocks = 256;    // blocks of the per-column statistics reduction
+// Column counts per bin in the global counters (after the CTR_COUNT work
+// counters): 0 = warp bins W and W2, 1 = CTA bin, 2 = global bin, 3 = bin H
+// (also included in 0's total when the statistics are read)
+constexpr int kBinHalf = 3;
+constexpr int kBinSlots = 4;
 
 // input checks, ||A||_1, statistics, scan, assembly
 __global__ void k_check_ptr(const int64_t *ptr, int64_t n, int64_t nnz, int32_t *err);
@@ -52,6 +57,9 @@ template <typename T> size_t work_bytes(const Caps &c);
 cudaError_t launch_bin_warp(int mode, bool fp32, int grid, int warps, const DevA &A, const DevParams &P,
                             const Caps &cap, const ColQueue &Q, const ColOut &O, const Frozen &F,
                             unsigned long long *gctr, bool last, cudaStream_t st);
+cudaError_t launch_bin_half(int mode, bool fp32, int grid, int warps, const DevA &A, const DevParams &P,
+                            const Caps &cap, const ColQueue &Q, const ColOut &O, const Frozen &F,
+                            unsigned long long *gctr, bool last, cudaStream_t st);
 cudaError_t launch_bin_block(int mode, bool fp32, int grid, const DevA &A, const DevParams &P, const Caps &cap,
                              const ColQueue &Q, const ColOut &O, const Frozen &F, unsigned long long *gctr,
                              bool last, char *gwork, size_t gstride, int bin, cudaStream_t st);
@@ -61,6 +69,7 @@ cudaError_t launch_adjoint_gather(int64_t n, int64_t nnzM, const int64_t *row_pt
                                   const double *poolR, const double *poolW, const double *alphaM,
                                   const double *xM, double *grad, cudaStream_t st);
 int occupancy_bin_warp(bool fp32, int warps, const Caps &cap);
+int occupancy_bin_half(bool fp32, int warps, const Caps &cap);
 int occupancy_bin_block(bool fp32, const Caps &cap, bool global_work);
 
 // apply / solver kernels (apply_kernels.cu)

@@ -51,9 +51,10 @@ struct rsai_handle {
     long long *bnc = nullptr, *bnnz = nullptr;
     int32_t *err = nullptr;
     // [0..3] queue counters of bins W, W2, C, G; [4..6] overflow counts W->W2,
-    // W2->C, C->G; [7] columns of a pool-overflow rerun
+    // W2->C, C->G; [7] columns of a pool-overflow rerun; [8] queue counter of
+    // bin H, [9] overflow count H->W
     uint32_t *qnext = nullptr;
-    int32_t *ovf1 = nullptr, *ovf2 = nullptr, *ovf3 = nullptr;
+    int32_t *ovf0 = nullptr, *ovf1 = nullptr, *ovf2 = nullptr, *ovf3 = nullptr;
     int32_t *ovf3_sorted = nullptr;  // the global bin's queue, largest column first
     uint8_t *cost_bucket = nullptr;
     uint32_t *cost_hist = nullptr;   // [kCostBuckets]
@@ -78,9 +79,9 @@ struct rsai_handle {
     size_t gstride = 0;
     int grid_g = 0;
     // bins
-    Caps capW{}, capW2{}, capC{}, capG{};
-    int grid_w = 0, grid_w2 = 0, warps_w2 = 0, grid_c = 0;
-    rsai_tuning tuning{4, 0, kSmallP, 0};
+    Caps capH{}, capW{}, capW2{}, capC{}, capG{};
+    int grid_h = 0, grid_w = 0, grid_w2 = 0, warps_w2 = 0, grid_c = 0;
+    rsai_tuning tuning{4, 0, kSmallP, 0, 0};
     // refit / backward scratch (allocated on first use)
     double *fval = nullptr, *fcval = nullptr;
     int64_t *qoff = nullptr, *Mcsr_to_csc = nullptr;
@@ -102,7 +103,7 @@ namespace {
 // layout of the scalar block (8-byte words); words 0 and 1 are unused since
 // ||A||_1 and the drop threshold moved to per-block arrays
 constexpr int kFrob2 = 2, kCtr = 3;
-constexpr int kCounts = kCtr + CTR_COUNT + 3;
+constexpr int kCounts = kCtr + CTR_COUNT + kBinSlots;
 constexpr int kPartial = kCounts + 2;
 constexpr int kScalars = kPartial + kStatBlocks;
 
@@ -198,6 +199,7 @@ DevParams dev_params(const rsai_handle *h) {
     P.drop_mode = h->params.drop_mode;
     P.precision = h->params.precision;
     P.init_a = (h->params.flags & RSAI_FLAG_INIT_PATTERN_A) ? 1 : 0;
+    P.spai = (h->params.flags & RSAI_FLAG_SELECT_SPAI) ? 1 : 0;
     P.eps = h->params.eps;
     P.tol = h->params.tol;
     P.tie_band = h->params.tie_band;
@@ -229,17 +231,26 @@ cudaError_t enqueue_bins(rsai_handle *h, int mode, const DevA &A, const Frozen &
                          const int32_t *wlist = nullptr, const uint32_t *wcount = nullptr) {
     const int64_t n = h->n;
     cudaMemsetAsync(h->qnext, 0, sizeof(uint32_t) * 7, st);  // queue and overflow counters; [7] = retry count
+    cudaMemsetAsync(h->qnext + 8, 0, sizeof(uint32_t) * 2, st);
     const DevParams P = dev_params(h);
     const bool fp32 = h->params.precision == RSAI_FP32_REFINE;
     ColOut O{h->col_off, h->col_len, h->col_q, h->rho, h->loops, h->flags, h->pool_rows, h->pool_vals,
              h->pool_cap, h->pool_top, h->err};
-    ColQueue QW{wlist, wcount, n, h->qnext + 0, h->ovf1, h->qnext + 4, h->ovf_cap};
+    // the first bin (H or W) takes the given list (or every column)
+    const bool use_h = h->tuning.half_bin != 0;
+    ColQueue QH{wlist, wcount, n, h->qnext + 8, h->ovf0, h->qnext + 9, h->ovf_cap};
+    ColQueue QW = use_h ? ColQueue{h->ovf0, h->qnext + 9, n, h->qnext + 0, h->ovf1, h->qnext + 4, h->ovf_cap}
+                        : ColQueue{wlist, wcount, n, h->qnext + 0, h->ovf1, h->qnext + 4, h->ovf_cap};
     ColQueue QW2{h->ovf1, h->qnext + 4, n, h->qnext + 1, h->ovf2, h->qnext + 5, h->ovf_cap};
     ColQueue QC{h->ovf2, h->qnext + 5, n, h->qnext + 2, h->ovf3, h->qnext + 6, h->ovf_cap};
     ColQueue QG{h->ovf3_sorted, h->qnext + 6, n, h->qnext + 3, nullptr, nullptr, 0};
     if (ev) cudaEventRecord(ev[1], st);
-    cudaError_t e = launch_bin_warp(mode, fp32, h->grid_w, h->tuning.warp_bin_warps, A, P, h->capW, QW, O, F, gctr,
-                                    false, st);
+    cudaError_t e = cudaSuccess;
+    if (use_h) {
+        e = launch_bin_half(mode, fp32, h->grid_h, h->tuning.warp_bin_warps, A, P, h->capH, QH, O, F, gctr, false, st);
+        if (e != cudaSuccess) return e;
+    }
+    e = launch_bin_warp(mode, fp32, h->grid_w, h->tuning.warp_bin_warps, A, P, h->capW, QW, O, F, gctr, false, st);
     if (e != cudaSuccess) return e;
     e = launch_bin_warp(mode, fp32, h->grid_w2, h->warps_w2, A, P, h->capW2, QW2, O, F, gctr, false, st);
     if (e != cudaSuccess) return e;
@@ -272,7 +283,7 @@ cudaError_t enqueue_build(rsai_handle *h, cudaStream_t st, cudaEvent_t *ev = nul
     if (ev) cudaEventRecord(ev[0], st);
     cudaMemsetAsync(h->dscal, 0, sizeof(unsigned long long) * kScalars, st);
     cudaMemsetAsync(h->err, 0, sizeof(int32_t), st);
-    cudaMemsetAsync(h->qnext, 0, sizeof(uint32_t) * 8, st);
+    cudaMemsetAsync(h->qnext, 0, sizeof(uint32_t) * 10, st);
     cudaMemsetAsync(h->pool_top, 0, sizeof(unsigned long long), st);
     cudaMemsetAsync(h->row_count, 0, sizeof(int32_t) * (size_t)n, st);
     cudaMemsetAsync(h->cursor, 0, sizeof(int32_t) * (size_t)n, st);
@@ -344,22 +355,44 @@ int plan_w2(rsai_handle *h, bool fp32) {
     return RSAI_OK;
 }
 
-// choose the capacities of the four bins from the device limits
+// launch shape of bin H: the warps per CTA of the warp bin (two columns per
+// warp), as many CTAs per SM as fit
+int plan_h(rsai_handle *h, bool fp32) {
+    const int occ0 = occupancy_bin_half(fp32, h->tuning.warp_bin_warps, h->capH);
+    if (occ0 < 1) return RSAI_ERR_CUDA;
+    const int occ = h->tuning.warp_bin_ctas_per_sm > 0 ? std::min(occ0, h->tuning.warp_bin_ctas_per_sm) : occ0;
+    h->grid_h = h->sms * occ;
+    return RSAI_OK;
+}
+
+#define TRY_PLAN(x)                        \
+    do {                                   \
+        const int rc_ = (x);               \
+        if (rc_ != RSAI_OK) return rc_;    \
+    } while (0)
+
+// choose the capacities of the five bins from the device limits
 int plan_bins(rsai_handle *h) {
     const bool fp32 = h->params.precision == RSAI_FP32_REFINE;
     int dev = h->device, max_optin = 0;
     cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int rneed = std::max(64, h->params.c * std::max(1, h->params.l_max));
-    h->capW = Caps{64, 32, 256, 64, 64 * 32, 64, h->tuning.small_qr_max_p, 0, 0, 64};
-    int occ = occupancy_bin_warp(fp32, h->tuning.warp_bin_warps, h->capW);
+    // bin H: half a warp per column, |I| <= 48, |J| <= 16 (the register QR's
+    // three rows per lane), sort buffers of 128 entries
+    const int spai = (h->params.flags & RSAI_FLAG_SELECT_SPAI) ? 1 : 0;
+    h->capH = Caps{48, 16, 128, 32, 48 * 16, 32, h->tuning.small_qr_max_p, 0, 0, 32, spai};
+    int occ = 0;
+    TRY_PLAN(plan_h(h, fp32));
+    h->capW = Caps{64, 32, 256, 64, 64 * 32, 64, h->tuning.small_qr_max_p, 0, 0, 64, spai};
+    occ = occupancy_bin_warp(fp32, h->tuning.warp_bin_warps, h->capW);
     if (occ < 1) return RSAI_ERR_CUDA;
     if (h->tuning.warp_bin_ctas_per_sm > 0) occ = std::min(occ, h->tuning.warp_bin_ctas_per_sm);
     h->grid_w = h->sms * occ;
     // bin W2: the warp bin's algorithm for |I| <= 128 (B 128 x 32), fewer warps per SM
-    h->capW2 = Caps{128, 32, 512, 64, 128 * 32, 64, h->tuning.small_qr_max_p, 0, 0, 128};
+    h->capW2 = Caps{128, 32, 512, 64, 128 * 32, 64, h->tuning.small_qr_max_p, 0, 0, 128, spai};
     if (plan_w2(h, fp32) != RSAI_OK) return RSAI_ERR_CUDA;
     // bin C: shared-memory workspace as large as the opt-in limit allows
-    Caps c{1024, 256, 4096, std::min(rneed * 2, 2048), 0, 0, 0, 0, 1, 1024};
+    Caps c{1024, 256, 4096, std::min(rneed * 2, 2048), 0, 0, 0, 0, 1, 1024, spai};
     size_t base = fp32 ? work_bytes<float>(c) : work_bytes<double>(c);
     size_t avail = (size_t)max_optin - 2048;
     if (base >= avail) return RSAI_ERR_CUDA;
@@ -369,7 +402,7 @@ int plan_bins(rsai_handle *h) {
     if (occ < 1) return RSAI_ERR_CUDA;
     h->grid_c = h->sms * occ;
     // bin G: a global-memory slab per CTA, one CTA per SM
-    h->capG = Caps{32768, 4096, 131072, 8192, (int64_t)1 << 24, 0, 0, max_optin - 2048, 1, 32768};
+    h->capG = Caps{32768, 4096, 131072, 8192, (int64_t)1 << 24, 0, 0, max_optin - 2048, 1, 32768, spai};
     h->gstride = ((fp32 ? work_bytes<float>(h->capG) : work_bytes<double>(h->capG)) + 255) & ~size_t(255);
     h->grid_g = 1;  // sized by the first build (size_global_slab)
     return RSAI_OK;
@@ -423,7 +456,7 @@ rsai_status rsai_params_check(const rsai_params *p) {
     if (!(p->tol >= 0.0) || !std::isfinite(p->tol)) return RSAI_ERR_INVALID_ARG;
     if (p->precision != RSAI_FP64 && p->precision != RSAI_FP32_REFINE) return RSAI_ERR_INVALID_ARG;
     if (!(p->tie_band >= 0.0) || !(p->tie_band < 1.0)) return RSAI_ERR_INVALID_ARG;
-    if (p->flags & ~(uint32_t)RSAI_FLAG_INIT_PATTERN_A) return RSAI_ERR_INVALID_ARG;
+    if (p->flags & ~(uint32_t)(RSAI_FLAG_INIT_PATTERN_A | RSAI_FLAG_SELECT_SPAI)) return RSAI_ERR_INVALID_ARG;
     return RSAI_OK;
 }
 
@@ -493,7 +526,8 @@ int build_common(rsai_handle *h, cudaStream_t st) {
     TRY(plan_bins(h));
     // ---- buffers of the build sequence ----
     h->ovf_cap = n;
-    TRY(dalloc(h, &h->qnext, 8, st));
+    TRY(dalloc(h, &h->qnext, 10, st));
+    TRY(dalloc(h, &h->ovf0, n, st));
     TRY(dalloc(h, &h->ovf1, n, st));
     TRY(dalloc(h, &h->ovf2, n, st));
     TRY(dalloc(h, &h->ovf3, n, st));
@@ -596,6 +630,13 @@ rsai_handle *new_handle(const rsai_params *params, cudaStream_t st) {
     cudaGetDevice(&h->device);
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
     h->params = *params;
+    // measured on the 64^3 convection-diffusion problem: FP64 builds run faster
+    // from the half-warp bin with the shared-memory QR, FP32+refine builds from
+    // the warp bin with the register QR (the autotuner revisits both)
+    if (params->precision == RSAI_FP64) {
+        h->tuning.half_bin = 1;
+        h->tuning.small_qr_max_p = 0;
+    }
     return h;
 }
 
@@ -828,6 +869,9 @@ rsai_status rsai_get_stats(rsai_handle *h, void *stream, rsai_stats *out) {
     out->n_nonfinite = (int64_t)c[CTR_NONFINITE];
     out->n_failed = (int64_t)c[CTR_FAILED];
     for (int b = 0; b < 3; ++b) out->cols_bin[b] = (int64_t)c[CTR_COUNT + b];
+    out->cols_bin[0] += (int64_t)c[CTR_COUNT + kBinHalf];
+    out->cols_bin_half = (int64_t)c[CTR_COUNT + kBinHalf];
+    out->select_flops = (double)c[CTR_SELECT];
     out->frob = std::sqrt(dbl(kFrob2));
     out->n_c = (int64_t)s[kCounts + 0];
     out->nnz_M = (int64_t)s[kCounts + 1];
@@ -938,10 +982,10 @@ int frozen_values(rsai_handle *h, const double *A_val, cudaStream_t st, DevA *ou
     if (!h->fval) {
         int rc = dalloc(h, &h->fval, h->nnz, st);
         if (rc == RSAI_OK) rc = dalloc(h, &h->fcval, h->nnz, st);
-        if (rc == RSAI_OK) rc = dalloc(h, &h->fctr, CTR_COUNT + 3, st);
+        if (rc == RSAI_OK) rc = dalloc(h, &h->fctr, CTR_COUNT + kBinSlots, st);
         if (rc != RSAI_OK) return rc;
     }
-    cudaMemsetAsync(h->fctr, 0, sizeof(unsigned long long) * (CTR_COUNT + 3), st);
+    cudaMemsetAsync(h->fctr, 0, sizeof(unsigned long long) * (CTR_COUNT + kBinSlots), st);
     if (cudaMemcpyAsync(h->fval, A_val, sizeof(double) * h->nnz, cudaMemcpyDefault, st) != cudaSuccess)
         return RSAI_ERR_CUDA;
     k_csc_from_csr<<<blocks(h->nnz, 256), 256, 0, st>>>(h->fval, h->csc_to_csr, h->fcval, h->nnz);
@@ -1059,7 +1103,7 @@ rsai_status rsai_set_tuning(rsai_handle *h, const rsai_tuning *t) {
     const int w = t->warp_bin_warps;
     if (w != 1 && w != 2 && w != 4 && w != 8) return RSAI_ERR_INVALID_ARG;
     if (t->warp_bin_ctas_per_sm < 0 || t->small_qr_max_p < 0 || t->small_qr_max_p > kSmallP ||
-        t->global_bin_ctas < 0)
+        t->global_bin_ctas < 0 || (t->half_bin != 0 && t->half_bin != 1))
         return RSAI_ERR_INVALID_ARG;
     cudaStream_t st = h->alloc_stream;
     if (cudaStreamSynchronize(st) != cudaSuccess) return RSAI_ERR_CUDA;
@@ -1067,12 +1111,15 @@ rsai_status rsai_set_tuning(rsai_handle *h, const rsai_tuning *t) {
     h->tuning = *t;
     const bool fp32 = h->params.precision == RSAI_FP32_REFINE;
     h->capW.small_p = t->small_qr_max_p;
+    h->capH.small_p = t->small_qr_max_p;
     int occ = occupancy_bin_warp(fp32, w, h->capW);
-    if (occ < 1) {
+    if (occ < 1 || occupancy_bin_half(fp32, w, h->capH) < 1) {
         h->tuning = old;
         h->capW.small_p = old.small_qr_max_p;
+        h->capH.small_p = old.small_qr_max_p;
         return RSAI_ERR_INVALID_ARG;
     }
+    if (plan_h(h, fp32) != RSAI_OK) return RSAI_ERR_CUDA;
     if (t->warp_bin_ctas_per_sm > 0) occ = std::min(occ, t->warp_bin_ctas_per_sm);
     h->grid_w = h->sms * occ;
     h->capW2.small_p = t->small_qr_max_p;

@@ -23,6 +23,7 @@ STATUS_NAMES = {
     13: "TOO_LARGE",
 }
 FLAG_INIT_PATTERN_A = 2  # RSAI_FLAG_INIT_PATTERN_A
+FLAG_SELECT_SPAI = 4  # RSAI_FLAG_SELECT_SPAI
 DROP = {"none": 0, "adaptive": 1, "fixed": 2}
 PRECISION = {"fp64": 0, "fp32_refine": 1}
 COL_CONVERGED, COL_RANK, COL_NONFINITE, COL_FAILED = 1, 2, 4, 8
@@ -62,7 +63,7 @@ class Params(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("warp_bin_warps", ctypes.c_int32), ("warp_bin_ctas_per_sm", ctypes.c_int32),
-                ("small_qr_max_p", ctypes.c_int32), ("global_bin_ctas", ctypes.c_int32)]
+                ("small_qr_max_p", ctypes.c_int32), ("global_bin_ctas", ctypes.c_int32), ("half_bin", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -76,7 +77,7 @@ class Stats(ctypes.Structure):
                 ("bytes", ctypes.c_double), ("loops", ctypes.c_int64), ("solves", ctypes.c_int64),
                 ("drops", ctypes.c_int64), ("p_max", ctypes.c_int32), ("q_max", ctypes.c_int32),
                 ("cols_bin", ctypes.c_int64 * 3), ("n_rank", ctypes.c_int64), ("n_nonfinite", ctypes.c_int64),
-                ("n_failed", ctypes.c_int64)]
+                ("n_failed", ctypes.c_int64), ("cols_bin_half", ctypes.c_int64), ("select_flops", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         d = {}
@@ -215,6 +216,9 @@ def default_params(**kw) -> Params:
         elif k == "init":
             # initial pattern J_k^(0) (Algorithm 1): "identity" ({k}) or "A" (rows of A(:,k))
             p.flags = (p.flags & ~FLAG_INIT_PATTERN_A) | (FLAG_INIT_PATTERN_A if v == "A" else 0)
+        elif k == "select":
+            # new indices: "rsai" (dominant rows, Algorithm 1) or "spai" (most profitable, Eqs. 2.5-2.7)
+            p.flags = (p.flags & ~FLAG_SELECT_SPAI) | (FLAG_SELECT_SPAI if v == "spai" else 0)
         else:
             setattr(p, k, v)
     return p
@@ -388,12 +392,12 @@ class Handle:
 
 
 def build(A, c=3, l_max=10, eps=0.3, drop="fixed", tol=1e-3, precision="fp64", tie_band=1e-12, stream=None,
-          allow_failed=False, init="identity") -> Handle:
+          allow_failed=False, init="identity", select="rsai") -> Handle:
     """rsai_build on a DeviceMatrix (device tensors) or a SparseMatrix-like
     object with numpy arrays (then the library copies from host memory)."""
     lib = load()
     params = default_params(c=c, l_max=l_max, eps=eps, drop=drop, tol=tol, precision=precision, tie_band=tie_band,
-                            init=init)
+                            init=init, select=select)
     if isinstance(A, DeviceMatrix):
         csr, csc, keep = A.csr(), A.csc(), None
     else:

@@ -37,10 +37,16 @@ def same_columns(cp, rows, ocp, orows):
     return same & ~bad
 
 
-def check_fp32_every_column(A, res, rho, ref, rtol_rho=1e-5, rtol_val=1e-6, max_mismatch=0.01, atol_rho=1e-14):
+def check_fp32_every_column(A, res, rho, ref, rtol_rho=1e-5, rtol_val=1e-6, max_mismatch=0.01, atol_rho=1e-12):
     """FP32+refine M (CSR triple `res`, per-column `rho`) against the oracle
     build `ref` on every column; returns the mask of columns whose pattern
-    equals the oracle's."""
+    equals the oracle's.
+
+    ||r_k|| is measured against ||e_k|| = 1.  A column whose pattern holds an
+    exact inverse column has rho ~ 0, where a relative bar means nothing: an
+    FP32 factorization corrected once in FP64 leaves a residual of about
+    (kappa(B) u_32)^2, so rho is held to an absolute floor of 1e-12 besides
+    the relative 1e-5."""
     cp, rows, vals = csc_of_csr(*res, A.n)
     same = same_columns(cp, rows, ref.colptr, ref.rows)
     assert same.mean() >= 1.0 - max_mismatch, f"{(~same).sum()} of {A.n} patterns differ"

@@ -32,7 +32,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.rsai_abi_version() == 1
+    assert lib.rsai_abi_version() == 2
     for code in range(0, 14):
         s = rsai.status_string(code)
         assert s and s != "unknown status"
@@ -44,7 +44,7 @@ def test_params_default_and_check(lib):
     assert (p.c, p.l_max, p.eps, p.drop_mode, p.tol, p.precision, p.tie_band) == (3, 10, 0.3, 2, 1e-3, 0, 1e-12)
     assert lib.rsai_params_check(ctypes.byref(p)) == 0
     bad = [dict(c=0), dict(c=33), dict(l_max=-1), dict(eps=0.0), dict(eps=float("nan")), dict(drop_mode=3),
-           dict(tol=-1.0), dict(precision=2), dict(tie_band=-1e-3), dict(tie_band=1.0), dict(flags=4)]
+           dict(tol=-1.0), dict(precision=2), dict(tie_band=-1e-3), dict(tie_band=1.0), dict(flags=1), dict(flags=8)]
     for b in bad:
         q = rsai.default_params()
         for k, v in b.items():
@@ -53,6 +53,8 @@ def test_params_default_and_check(lib):
     assert lib.rsai_params_check(None) == 1
     ok = rsai.default_params(init="A")
     assert ok.flags == rsai.FLAG_INIT_PATTERN_A and lib.rsai_params_check(ctypes.byref(ok)) == 0
+    ok = rsai.default_params(init="A", select="spai")
+    assert ok.flags == rsai.FLAG_INIT_PATTERN_A | rsai.FLAG_SELECT_SPAI and lib.rsai_params_check(ctypes.byref(ok)) == 0
 
 
 def test_null_arguments_rejected_without_device(lib):

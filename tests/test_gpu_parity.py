@@ -114,6 +114,21 @@ def test_fp32_refine_bicgstab_iterations_within_one(which):
     h.free()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_more_dominant_rows_than_a_team_has_lanes(c1, precision):
+    """c = 24 dominant rows per loop: more rows of R-hat than the 16 lanes of
+    the half-warp bin (and close to the 32 of a warp), so the rows of A(R-hat,:)
+    are read in several passes.  Same bar as the configurations' parity."""
+    kw = dict(c=24, l_max=3, eps=0.05, tol=1e-3, drop="fixed")
+    h, dA, res, rho, loops, flags, st = gpu_M(c1, precision=precision, **kw)
+    ref = oracle.build(c1, **kw)
+    if precision == "fp64":
+        assert_fp64_parity(c1, ref, res, rho, loops, flags, st)
+    else:
+        check_fp32_every_column(c1, res, rho, ref)
+    h.free()
+
+
 def test_power_of_two_scaling_gpu(c1):
     a = gpu_M(c1, drop="fixed", precision="fp64", **PARAMS_C1)
     b = gpu_M(c1.with_values(c1.val * 8.0), drop="fixed", precision="fp64", **PARAMS_C1)
@@ -289,14 +304,18 @@ def test_tuning_changes_speed_not_results(c1):
                 h.rebuild()
                 for a, b in zip(ref, h.M()):
                     assert torch.equal(a, b), (precision, tun)
-            for sp in (0, 8):
-                h.set_tuning(small_qr_max_p=sp)
+            # the QR variant and the first bin (half warp or warp per column) change the rounding only
+            tol = 1e-12 if precision == "fp64" else 1e-6
+            for tun in (dict(small_qr_max_p=0), dict(small_qr_max_p=8), dict(half_bin=0), dict(half_bin=1)):
+                h.set_tuning(**tun)
                 h.rebuild()
                 rp, ci, va = h.M()
-                assert torch.equal(rp, ref[0]) and torch.equal(ci, ref[1])
-                tol = 1e-12 if precision == "fp64" else 1e-6
+                assert torch.equal(rp, ref[0]) and torch.equal(ci, ref[1]), (precision, tun)
                 np.testing.assert_allclose(va.cpu().numpy(), ref[2].cpu().numpy(), rtol=tol,
                                            atol=tol * float(ref[2].abs().max()))
+            h.set_tuning(half_bin=1)
+            h.rebuild()
+            assert h.stats()["cols_bin_half"] > 0
             h.free()
 
 
