@@ -103,7 +103,7 @@ class ClockSampler:
             q = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-            cmd = ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"]
+            cmd = ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "50"]
             if self.uuid:
                 cmd += ["-i", self.uuid]
             self.f = open(self.path, "w")
@@ -215,6 +215,65 @@ def run_oracle_sample(A, threads: int, stride: int):
     return len(cols), dt, M
 
 
+SPAI_KEYS = ("select", "l_max", "drop", "spar", "frob", "n_c", "build_ms", "first_build_s", "bicgstab_iters",
+             "bicgstab_s", "qr_flops", "select_flops")
+
+
+def powerlaw_1e6_extra(torch, np, rsai, inputs):
+    """The n = 1e6 power law (c = 5, l_max = 8, eps = 0.4, FIXED tol = 1e-3),
+    FP32+refine: the first build (allocation, checks and build, wall clock),
+    one graph-replayed rebuild (CUDA events), the bins' split, and ||r_k|| of
+    256 random columns against the FP64 oracle.  There is no FP64 GPU build of
+    this workload here: its ~3e14 FP64 flops need more than 280 s at the GPU's
+    FP64 rate."""
+    import oracle
+
+    kw = dict(c=5, l_max=8, eps=0.4, tol=1e-3, drop="fixed")
+    P = inputs.powerlaw(1000000, seed=1503)
+    dP = rsai.DeviceMatrix.from_host(P)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = rsai.build(dP, precision="fp32_refine", **kw)
+    torch.cuda.synchronize()
+    first_s = time.perf_counter() - t0
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    h.rebuild()
+    e1.record(st)
+    torch.cuda.synchronize()
+    rebuild_ms = e0.elapsed_time(e1)
+    s = h.stats()
+    rho = h.columns()[0].cpu().numpy()
+    ph = h.phase_times()
+    h.free()
+    cols = np.sort(np.random.default_rng(1503).choice(P.n, 256, replace=False))
+    t1 = time.perf_counter()
+    ref = oracle.build(P, cols=cols, **kw)
+    osec = time.perf_counter() - t1
+    rel = np.abs(rho[cols] - ref.rho) / np.maximum(ref.rho, 1e-300)
+    return {"workload": "powerlaw_n1e6_seed1503", "n": P.n, "nnz": P.nnz, **kw, "precision": "fp32_refine",
+            "first_build_s": first_s, "first_build_columns_per_s": P.n / first_s, "rebuild_ms": rebuild_ms,
+            "rebuild_columns_per_s": P.n / (rebuild_ms / 1e3), "phases_ms": ph, "cols_bin": s["cols_bin"],
+            "frob": s["frob"], "nnz_M": s["nnz_M"], "n_c": s["n_c"], "n_failed": s["n_failed"],
+            "qr_flops": s["qr_flops"], "p_max": s["p_max"], "q_max": s["q_max"],
+            "oracle_sample": {"columns": len(cols), "max_rel_rho_diff": float(rel.max()),
+                              "within_1e-5": int((rel <= 1e-5).sum()), "oracle_s": osec},
+            "fp64_gpu_build": "omitted: ~3e14 FP64 flops, over 280 s at the GPU's FP64 rate"}
+
+
+def batch_extra(members):
+    """`members` of the 512-member batch (half convection-diffusion, half power
+    law, n uniform in [1000, 50000]) in one graph-replayed build, FP32+refine,
+    with the backward on the frozen pattern and each member's ||A_b M_b - I||_F
+    against the FP64 build of the same batch."""
+    from paper_1503_04500_gb300 import sweep
+
+    r = sweep.run_batch(count=members, nmax=50000, precision="fp32_refine", rebuilds=1)
+    r["members_of_512"] = members
+    return r
+
+
 def reference_arm(args):
     """The FP64 CPU oracle as it stands, on the host cores (rank 0 only)."""
     rank, world, _ = dist_env()
@@ -255,7 +314,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-extras", dest="extras", action="store_false",
-                    help="skip the parametric 256^2 forward/adjoint measurement")
+                    help="skip every measurement besides the 64^3 workload")
+    ap.add_argument("--no-large", dest="large", action="store_false",
+                    help="skip the n = 1e6 power law, the batch and the SPAI comparison (a few minutes)")
+    ap.add_argument("--batch-members", type=int, default=8,
+                    help="members of the 512-member batch configuration built in the batch measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -493,6 +556,19 @@ def main():
                                      "fwd_bwd_ms": statistics.median(lt["fwd_bwd"])}
             h4.free()
 
+    # the uneven-size configurations: the n = 1e6 power law and a batch of the 512-member set
+    c3 = c5 = spai_cmp = None
+    if args.extras and args.large:
+        c3 = powerlaw_1e6_extra(torch, np, rsai, inputs)
+        c5 = batch_extra(args.batch_members)
+        from paper_1503_04500_gb300 import sweep
+
+        spai_cmp = {}
+        for wl, size in (("convdiff3d", 32), ("powerlaw", 20000)):
+            r = sweep.compare_spai(wl, size, precision="fp64", rebuilds=1)
+            spai_cmp[f"{wl}_{size}"] = {"rsai": {k: r["rsai"][k] for k in SPAI_KEYS},
+                                        "spai": {k: r["spai"][k] for k in SPAI_KEYS}, **r["ratio"]}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -521,9 +597,10 @@ def main():
         "bwd_ms": bwd32, "bwd_fwd_ratio_fp64": bwd64 / dev_ms64,
         "roofline": roof32, "phases_ms": ph32,
         "tuning": {"fp32_refine": tuned32["tuning"], "fp64": tuned64["tuning"]},
-        "parametric2d_256": c4,
+        "parametric2d_256": c4, "powerlaw_1e6": c3, "batch": c5, "rsai_vs_spai": spai_cmp,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "gpu_launches": KERNELS_PER_BUILD * args.steps,
+        # the half-warp bin adds one launch when the tuned shape uses it
+        "gpu_launches": (KERNELS_PER_BUILD + int(tuned32["tuning"].get("half_bin", 0))) * args.steps,
         "wall_s_timed_region": t_wall,
     }
     if rank == 0:

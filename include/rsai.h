@@ -326,10 +326,11 @@ rsai_status rsai_bicgstab_noalloc(const rsai_csr *A, const rsai_csr *M, const do
  * (paper_1503_04500_gb300/autotune.py).
  */
 typedef struct {
-    int32_t warp_bin_warps;       /* warps per CTA of the warp bin: 1, 2, 4 or 8 (default 4); the second
+    int32_t warp_bin_warps;       /* warps per CTA of the warp bin: 1, 2, 4 or 8 (default 8); the second
                                      warp bin (|I| <= 128) uses it halved until its workspace fits */
     int32_t warp_bin_ctas_per_sm; /* resident CTAs per SM of the warp bin, 0 = as many as fit */
-    int32_t small_qr_max_p;       /* largest |J| solved by the register-resident warp QR, 0..16 (16) */
+    int32_t small_qr_max_p;       /* largest |J| solved by the register-resident warp QR, 0..16
+                                     (default 16; 8 for RSAI_FP64) */
     int32_t global_bin_ctas;      /* CTAs of the global bin, 0 = one per column that reaches it, <= SMs */
     int32_t half_bin;             /* 1: columns start in the half-warp bin (two columns per warp, |I| <= 48,
                                      |J| <= 16) and move on to the warp bin when they outgrow it; 0: they start

@@ -81,7 +81,7 @@ struct rsai_handle {
     // bins
     Caps capH{}, capW{}, capW2{}, capC{}, capG{};
     int grid_h = 0, grid_w = 0, grid_w2 = 0, warps_w2 = 0, grid_c = 0;
-    rsai_tuning tuning{4, 0, kSmallP, 0, 0};
+    rsai_tuning tuning{8, 0, kSmallP, 0, 0};
     // refit / backward scratch (allocated on first use)
     double *fval = nullptr, *fcval = nullptr;
     int64_t *qoff = nullptr, *Mcsr_to_csc = nullptr;
@@ -630,12 +630,12 @@ rsai_handle *new_handle(const rsai_params *params, cudaStream_t st) {
     cudaGetDevice(&h->device);
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
     h->params = *params;
-    // measured on the 64^3 convection-diffusion problem: FP64 builds run faster
-    // from the half-warp bin with the shared-memory QR, FP32+refine builds from
-    // the warp bin with the register QR (the autotuner revisits both)
+    // the shapes the autotuner picks on the 64^3 convection-diffusion problem:
+    // FP64 builds start in the half-warp bin with the register QR up to
+    // |J| = 8, FP32+refine builds in the warp bin with the register QR up to 16
     if (params->precision == RSAI_FP64) {
         h->tuning.half_bin = 1;
-        h->tuning.small_qr_max_p = 0;
+        h->tuning.small_qr_max_p = 8;
     }
     return h;
 }

@@ -6,6 +6,7 @@ built on Aᵀ by the same kernels).
     python -m paper_1503_04500_gb300.sweep --workload convdiff3d --size 32 \
         --eps 0.2,0.3,0.4 --c 3,5 --lmax 5,10 --precision fp32_refine
     python -m paper_1503_04500_gb300.sweep --batch 64 --size 5000 --precision fp32_refine
+    python -m paper_1503_04500_gb300.sweep --compare-spai --workload powerlaw --size 20000
 
 One JSON line per setting: spar = nnz(M)/nnz(A), ||AM - I||_F (or ||MA - I||_F),
 n_c (columns with ||r_k|| > ε), the build time (median of graph-replayed
@@ -44,16 +45,16 @@ def _ints(s: str):
 
 
 def run(workload="convdiff2d", size=20, seed=1503, eps=(0.3,), c=(3,), lmax=(10,), drop="fixed", tol=1e-3,
-        precision="fp64", side="right", rebuilds=5, solve=True, init="identity"):
+        precision="fp64", side="right", rebuilds=5, solve=True, init="identity", select="rsai", A=None):
     """Yield one result dict per (eps, c, l_max) setting."""
     import torch
 
-    A = _workload(workload, size, seed)
+    A = A if A is not None else _workload(workload, size, seed)
     dA = rsai.DeviceMatrix.from_host(A)
     b = torch.as_tensor(inputs.ones_rhs(A), device="cuda")
     st = torch.cuda.current_stream()
     for e, cc, lm in itertools.product(eps, c, lmax):
-        kw = dict(c=cc, l_max=lm, eps=e, drop=drop, tol=tol, precision=precision, init=init)
+        kw = dict(c=cc, l_max=lm, eps=e, drop=drop, tol=tol, precision=precision, init=init, select=select)
         t0 = time.perf_counter()
         h = rsai.build_left(dA, **kw) if side == "left" else rsai.build(dA, **kw)
         torch.cuda.synchronize()
@@ -70,9 +71,10 @@ def run(workload="convdiff2d", size=20, seed=1503, eps=(0.3,), c=(3,), lmax=(10,
             times.append(e0.elapsed_time(e1))
         s = h.stats()
         out = {"workload": workload, "n": A.n, "nnz_A": A.nnz, "side": side, "init": init, "precision": precision,
-               "eps": e,
+               "select": select, "eps": e,
                "c": cc, "l_max": lm, "drop": drop, "tol": tol, "spar": s["nnz_M"] / A.nnz, "frob": s["frob"],
                "n_c": s["n_c"], "p_max": s["p_max"], "q_max": s["q_max"], "cols_bin": s["cols_bin"],
+               "qr_flops": s["qr_flops"], "select_flops": s["select_flops"], "loops": s["loops"],
                "build_ms": statistics.median(times) if times else None, "first_build_s": first_s,
                "phases_ms": right.phase_times()}
         if solve and side == "right":
@@ -83,6 +85,28 @@ def run(workload="convdiff2d", size=20, seed=1503, eps=(0.3,), c=(3,), lmax=(10,
                         "bicgstab_s": time.perf_counter() - t1})
         h.free()
         yield out
+
+
+def compare_spai(workload="powerlaw", size=20000, seed=1503, precision="fp64", rebuilds=5, A=None):
+    """RSAI(tol) against SPAI on one synthetic matrix, with Section 5.2's
+    settings (the analogue of its table): RSAI(tol) with eps = 0.3, c = 3,
+    l_max = 10 and the drop of Eq. 4.3 (FIXED tol = 1e-3 on A/||A||_1); SPAI
+    with the same eps, three most profitable indices per loop, no dropping and
+    l_max = floor(10 nnz(A) / (3 n)) (which keeps nnz(M)/nnz(A) <= 5).  Returns
+    both rows (spar, build time, n_c, BiCGStab iterations and time) and the
+    ratios SPAI / RSAI(tol) of build time and iterations."""
+    import math
+
+    A = A if A is not None else _workload(workload, size, seed)
+    lm_spai = int(math.floor(10 * A.nnz / (3 * A.n)))
+    r = next(run(workload, size, seed, (0.3,), (3,), (10,), "fixed", 1e-3, precision, "right", rebuilds, True,
+                 "identity", "rsai", A))
+    sp = next(run(workload, size, seed, (0.3,), (3,), (lm_spai,), "none", 1e-3, precision, "right", rebuilds, True,
+                  "identity", "spai", A))
+    ratio = {"build_time_spai_over_rsai": sp["build_ms"] / r["build_ms"] if r["build_ms"] else None,
+             "iters_spai_over_rsai": (sp["bicgstab_iters"] / r["bicgstab_iters"]) if r.get("bicgstab_iters") else None,
+             "n_c_rsai": r["n_c"], "n_c_spai": sp["n_c"], "spar_rsai": r["spar"], "spar_spai": sp["spar"]}
+    return {"rsai": r, "spai": sp, "ratio": ratio}
 
 
 def run_batch(count=64, nmax=5000, precision="fp32_refine", c=3, l_max=10, eps=0.3, drop="fixed", tol=1e-3,
@@ -156,15 +180,22 @@ def main(argv=None):
     ap.add_argument("--no-solve", dest="solve", action="store_false")
     ap.add_argument("--init", default="identity", choices=["identity", "A"],
                     help="initial pattern J_k^(0): {k} or the rows of column k of A")
+    ap.add_argument("--select", default="rsai", choices=["rsai", "spai"],
+                    help="new indices: dominant rows (Algorithm 1) or SPAI's most profitable (Eqs. 2.5-2.7)")
+    ap.add_argument("--compare-spai", action="store_true",
+                    help="instead of a sweep: RSAI(tol) against SPAI with Section 5.2's settings")
     ap.add_argument("--batch", type=int, default=0,
                     help="instead of a sweep: a batch of this many random members (n up to --size) in one build")
     a = ap.parse_args(argv)
+    if a.compare_spai:
+        print(json.dumps(compare_spai(a.workload, a.size, a.seed, a.precision, max(a.rebuilds, 1))), flush=True)
+        return
     if a.batch > 0:
         print(json.dumps(run_batch(a.batch, a.size, a.precision, _ints(a.c)[0], _ints(a.lmax)[0], _floats(a.eps)[0],
                                    a.drop, a.tol, max(a.rebuilds, 1))), flush=True)
         return
     for row in run(a.workload, a.size, a.seed, _floats(a.eps), _ints(a.c), _ints(a.lmax), a.drop, a.tol,
-                   a.precision, a.side, a.rebuilds, a.solve, a.init):
+                   a.precision, a.side, a.rebuilds, a.solve, a.init, a.select):
         print(json.dumps(row), flush=True)
 
 
