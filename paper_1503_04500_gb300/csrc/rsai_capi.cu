@@ -552,7 +552,11 @@ int build_common(rsai_handle *h, cudaStream_t st) {
     {
         // result pool: if columns find it full, it grows (keeping what was
         // written) and only those columns run again
-        const int64_t g_est = std::max<int64_t>(32, 6 * (nnz / std::max<int64_t>(1, n)) + 16);
+        // 10 entries per nonzero of an average column of A, plus 16: above
+        // the nnz(M)/n of the configurations (15.5 on the 64^3 problem, 78 on
+        // the n = 1e6 power law, where 6 per nonzero made part of the first
+        // build run twice)
+        const int64_t g_est = std::max<int64_t>(32, 10 * (nnz / std::max<int64_t>(1, n)) + 16);
         int64_t cap = std::min<int64_t>(n * g_est, n * n);
         h->pool_cap = cap;
         TRY(dalloc(h, &h->pool_rows, cap, st));
