@@ -600,7 +600,8 @@ def main():
         "parametric2d_256": c4, "powerlaw_1e6": c3, "batch": c5, "rsai_vs_spai": spai_cmp,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         # the half-warp bin adds one launch when the tuned shape uses it
-        "gpu_launches": (KERNELS_PER_BUILD + int(tuned32["tuning"].get("half_bin", 0))) * args.steps,
+        # (+1: the FP32 copy of A's values that an FP32+refine build makes)
+        "gpu_launches": (KERNELS_PER_BUILD + 1 + int(tuned32["tuning"].get("half_bin", 0))) * args.steps,
         "wall_s_timed_region": t_wall,
     }
     if rank == 0:

@@ -900,9 +900,10 @@ template <class Team, typename T> struct Column {
             }
             if (row == k) acc -= 1.0;
             w.r[i] = acc;
-            ss = fma(acc, acc, ss);
+            if (!refine) ss = fma(acc, acc, ss);
         }
-        rho = sqrt(team.sum(ss));
+        // the refinement step reads r only; its norm is not formed
+        if (!refine) rho = sqrt(team.sum(ss));
         long long nnzJ = team.sum(cnt);
         if (refine) c_ref64 += 2 * nnzJ + 2 * (long long)s;
         else c_res += 2 * nnzJ + 2 * (long long)s;
@@ -971,16 +972,16 @@ template <class Team, typename T> struct Column {
             T *Bc = w.B + (int64_t)c * q;
             for (int64_t e = e0; e < e1; e += 4) {
                 int32_t ri[4];
-                double av[4];
+                T av[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     ri[u] = (e + u < e1) ? A.row_idx[e + u] : -1;
-                    av[u] = (e + u < e1) ? A.cval[e + u] : 0.0;
+                    av[u] = (e + u < e1) ? csc_value<T>(A, e + u) : T(0);
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     if (ri[u] >= 0) {
-                        T a = (T)av[u];
+                        const T a = av[u];
                         Bc[find_i32(w.I, q, ri[u])] = a;
                         fro2 += a * a;
                     }
@@ -1090,7 +1091,7 @@ template <class Team, typename T> struct Column {
             const int32_t j = w.Jn[b];
             T *Bc = w.B + (int64_t)(po + b) * q;
             for (int64_t e = A.col_ptr[j]; e < A.col_ptr[j + 1]; ++e) {
-                const T a = (T)A.cval[e];
+                const T a = csc_value<T>(A, e);
                 const int ii = find_i32(w.I, q, A.row_idx[e]);
                 if (ii >= 0) Bc[w.Ip[ii]] = a;
                 fro2 += a * a;
@@ -1359,7 +1360,6 @@ template <class Team, typename T> struct Column {
         c_bytes += team.sum(b);
     }
 
-    // Runs the whole column.  Returns COL_DONE or COL_OVERFLOW.
     // ---- frozen pattern (refit, backward) ----
 
     // J = Jk (sorted, length pk): false if it does not fit this bin
@@ -1484,16 +1484,19 @@ template <class Team, typename T> struct Column {
         const int64_t e0 = A.col_ptr[k];
         const int len = (int)(A.col_ptr[k + 1] - e0);
         if (len > cap.qcap) return false;
-        double nn = 0.0, akk = 0.0;
+        double nn = 0.0;
+        int kpos = -1;
         for (int i = me; i < len; i += Team::SIZE) {
             const int32_t r = A.row_idx[e0 + i];
             const double a = A.cval[e0 + i];
             w.I[i] = r;
             nn = fma(a, a, nn);
-            if (r == k) akk = a;
+            if (r == k) kpos = i;
         }
         nn = team.sum(nn);
-        akk = team.sum(akk);
+        // a_kk found by its position (an integer reduction), not summed in double
+        kpos = team.maxv(kpos);
+        const double akk = kpos >= 0 ? A.cval[e0 + kpos] : 0.0;
         q = len;
         build_jhash();
         if (me == 0) w.m[0] = (nn > 0.0) ? akk / nn : 0.0;

@@ -27,7 +27,16 @@ struct DevA {
     const int64_t *col_ptr;
     const int32_t *row_idx;
     const double *cval;
+    const float *cval32;  // FP32 copy of cval for the FP32 QR's gathers (NULL: convert on load)
 };
+
+// A(i,j) of CSC entry e in the QR's precision.  The FP32 copy holds the same
+// round-to-nearest values that a conversion on load would give.
+template <typename T> __device__ __forceinline__ T csc_value(const DevA &A, int64_t e);
+template <> __device__ __forceinline__ double csc_value<double>(const DevA &A, int64_t e) { return A.cval[e]; }
+template <> __device__ __forceinline__ float csc_value<float>(const DevA &A, int64_t e) {
+    return A.cval32 ? A.cval32[e] : __double2float_rn(A.cval[e]);
+}
 
 // Parameters as the kernels see them (rsai_params plus derived values).
 struct DevParams {

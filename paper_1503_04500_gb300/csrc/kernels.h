@@ -19,6 +19,7 @@ __global__ void k_check_ptr(const int64_t *ptr, int64_t n, int64_t nnz, int32_t 
 __global__ void k_check_idx(const int64_t *ptr, const int32_t *idx, int64_t n, int32_t *err, int empty_is_error);
 __global__ void k_csc_map(DevA A, int64_t *csc_to_csr, int32_t *err);
 __global__ void k_csc_from_csr(const double *csr_val, const int64_t *csc_to_csr, double *cval, int64_t nnz);
+__global__ void k_to_f32(const double *in, float *out, int64_t n);
 __global__ void k_norm1(const int64_t *col_ptr, const double *cval, int64_t n, const int32_t *col_block,
                         double *out);
 __global__ void k_collect_failed(const int32_t *flags, int64_t n, int32_t *list, uint32_t *count);

@@ -38,6 +38,7 @@ struct rsai_handle {
     int64_t *row_ptr = nullptr, *col_ptr = nullptr, *csc_to_csr = nullptr;
     int32_t *col_idx = nullptr, *row_idx = nullptr;
     double *val = nullptr, *cval = nullptr;
+    float *cval32 = nullptr;  // FP32 copy of cval (FP32_REFINE builds), refreshed by every build
     // 8-byte words: (unused), (unused), frob2, counters, column counts, partial sums
     unsigned long long *dscal = nullptr;
     // blocks (a batch of independent matrices as one block-diagonal matrix)
@@ -189,7 +190,7 @@ cudaError_t to_device(void *dst, const void *src, size_t bytes, cudaStream_t st)
 }
 
 DevA dev_a(const rsai_handle *h) {
-    return DevA{h->n, h->row_ptr, h->col_idx, h->val, h->col_ptr, h->row_idx, h->cval};
+    return DevA{h->n, h->row_ptr, h->col_idx, h->val, h->col_ptr, h->row_idx, h->cval, h->cval32};
 }
 
 DevParams dev_params(const rsai_handle *h) {
@@ -289,6 +290,7 @@ cudaError_t enqueue_build(rsai_handle *h, cudaStream_t st, cudaEvent_t *ev = nul
     cudaMemsetAsync(h->cursor, 0, sizeof(int32_t) * (size_t)n, st);
     cudaMemsetAsync(h->norm1_arr, 0, sizeof(double) * (size_t)h->nblocks, st);
     k_norm1<<<blocks(n, 256), 256, 0, st>>>(h->col_ptr, h->cval, n, h->col_block, h->norm1_arr);
+    if (h->cval32) k_to_f32<<<blocks(h->nnz, 256), 256, 0, st>>>(h->cval, h->cval32, h->nnz);
     k_tau_fixed<<<blocks(h->nblocks, 256), 256, 0, st>>>(h->norm1_arr, h->params.tol, h->tau_arr, h->nblocks);
 
     cudaError_t e = enqueue_bins(h, MODE_BUILD, dev_a(h), Frozen{}, h->dscal + kCtr, st, ev, hook);
@@ -524,6 +526,7 @@ int build_common(rsai_handle *h, cudaStream_t st) {
         TRY(herr);
     }
     TRY(plan_bins(h));
+    if (h->params.precision == RSAI_FP32_REFINE) TRY(dalloc(h, &h->cval32, nnz, st));
     // ---- buffers of the build sequence ----
     h->ovf_cap = n;
     TRY(dalloc(h, &h->qnext, 10, st));
@@ -993,7 +996,7 @@ int frozen_values(rsai_handle *h, const double *A_val, cudaStream_t st, DevA *ou
     if (cudaMemcpyAsync(h->fval, A_val, sizeof(double) * h->nnz, cudaMemcpyDefault, st) != cudaSuccess)
         return RSAI_ERR_CUDA;
     k_csc_from_csr<<<blocks(h->nnz, 256), 256, 0, st>>>(h->fval, h->csc_to_csr, h->fcval, h->nnz);
-    *out = DevA{h->n, h->row_ptr, h->col_idx, h->fval, h->col_ptr, h->row_idx, h->fcval};
+    *out = DevA{h->n, h->row_ptr, h->col_idx, h->fval, h->col_ptr, h->row_idx, h->fcval, nullptr};
     return cuda_status(cudaGetLastError());
 }
 

@@ -58,6 +58,12 @@ __global__ void k_csc_from_csr(const double *csr_val, const int64_t *csc_to_csr,
     if (e < nnz) cval[e] = csr_val[csc_to_csr[e]];
 }
 
+// out = in rounded to float (round to nearest), the FP32 QR's copy of A's values
+__global__ void k_to_f32(const double *in, float *out, int64_t n) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < n) out[e] = __double2float_rn(in[e]);
+}
+
 // ||A||_1 = max_j sum_i |a_ij| (Eq. 4.3), per block of columns; nonnegative
 // doubles order like their bits
 // ||A||_1 per block: the column abs-sums, max-combined as the bit patterns of
