@@ -15,9 +15,22 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.h"
 
 using namespace rsai;
+
+namespace {
+// A named range on the host timeline of a profiler (NVTX; nothing happens
+// unless a tool is attached): the phases of the entry points below.
+struct Nvtx {
+    explicit Nvtx(const char *name) { nvtxRangePushA(name); }
+    ~Nvtx() { nvtxRangePop(); }
+    Nvtx(const Nvtx &) = delete;
+    Nvtx &operator=(const Nvtx &) = delete;
+};
+}  // namespace
 
 namespace {
 // device memory source: a caller's allocator, or the CUDA stream-ordered one
@@ -512,6 +525,7 @@ int build_common(rsai_handle *h, cudaStream_t st) {
     // the pointer checks returns at once if an earlier one set the error word,
     // so it never follows an index that was not checked.
     {
+        Nvtx range("rsai: check A");
         int32_t herr = 0;
         cudaMemsetAsync(h->err, 0, sizeof(int32_t), st);
         k_check_ptr<<<blocks(n + 1, 256), 256, 0, st>>>(h->row_ptr, n, nnz, h->err);
@@ -525,7 +539,10 @@ int build_common(rsai_handle *h, cudaStream_t st) {
             return RSAI_ERR_CUDA;
         TRY(herr);
     }
-    TRY(plan_bins(h));
+    {
+        Nvtx range("rsai: plan bins");
+        TRY(plan_bins(h));
+    }
     if (h->params.precision == RSAI_FP32_REFINE) TRY(dalloc(h, &h->cval32, nnz, st));
     // ---- buffers of the build sequence ----
     h->ovf_cap = n;
@@ -553,6 +570,7 @@ int build_common(rsai_handle *h, cudaStream_t st) {
     TRY(dalloc(h, &h->gwork, h->gstride * (size_t)h->grid_g, st));
     int status = RSAI_OK;
     {
+        Nvtx range("rsai: first build");
         // result pool: if columns find it full, it grows (keeping what was
         // written) and only those columns run again
         // 10 entries per nonzero of an average column of A, plus 16: above
@@ -662,6 +680,7 @@ extern "C" {
 
 rsai_status rsai_build(const rsai_csr *A, const rsai_csc *Acsc, const rsai_params *params, void *stream,
                        rsai_handle **out) {
+    Nvtx range("rsai_build");
     if (!out) return RSAI_ERR_INVALID_ARG;
     *out = nullptr;
     int rc = rsai_params_check(params);
@@ -710,6 +729,7 @@ rsai_status rsai_build(const rsai_csr *A, const rsai_csc *Acsc, const rsai_param
 
 rsai_status rsai_build_batch(const rsai_csr *As, const rsai_csc *Acscs, int32_t count, const rsai_params *params,
                              void *stream, rsai_handle **out) {
+    Nvtx range("rsai_build_batch");
     if (!out) return RSAI_ERR_INVALID_ARG;
     *out = nullptr;
     if (!As || !Acscs || count < 1) return RSAI_ERR_INVALID_ARG;
@@ -814,6 +834,7 @@ rsai_status rsai_set_values(rsai_handle *h, const double *A_val, void *stream) {
 }
 
 rsai_status rsai_rebuild(rsai_handle *h, void *stream) {
+    Nvtx range("rsai_rebuild");
     if (!h) return RSAI_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     if (!h->graph) {
@@ -957,6 +978,7 @@ rsai_status rsai_apply(rsai_handle *h, const double *x, double *y, void *stream)
 
 rsai_status rsai_bicgstab(const rsai_csr *A, rsai_handle *M, const double *b, double *x, double rtol, int32_t maxit,
                           int32_t *iters, double *relres, void *stream) {
+    Nvtx range("rsai_bicgstab");
     int rc = check_csr_host(A);
     if (rc != RSAI_OK) return (rsai_status)rc;
     if (!b || !x || !iters || !relres || maxit < 0 || !(rtol > 0.0)) return RSAI_ERR_INVALID_ARG;
@@ -1020,6 +1042,7 @@ int finish_frozen(rsai_handle *h, cudaStream_t st) {
 extern "C" {
 
 rsai_status rsai_refit(rsai_handle *h, const double *A_val, double *M_val, double *rho2, void *stream) {
+    Nvtx range("rsai_refit");
     if (!h || !A_val) return RSAI_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nnzM = nnz_of_M(h, st);
@@ -1051,6 +1074,7 @@ rsai_status rsai_refit(rsai_handle *h, const double *A_val, double *M_val, doubl
 
 rsai_status rsai_backward(rsai_handle *h, const double *A_val, const double *grad_M, const double *grad_rho2,
                           double *grad_A, void *stream) {
+    Nvtx range("rsai_backward");
     if (!h || !A_val || !grad_M || !grad_A) return RSAI_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nnzM = nnz_of_M(h, st);
