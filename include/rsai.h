@@ -331,7 +331,9 @@ typedef struct {
     int32_t warp_bin_ctas_per_sm; /* resident CTAs per SM of the warp bin, 0 = as many as fit */
     int32_t small_qr_max_p;       /* largest |J| solved by the register-resident warp QR, 0..16
                                      (default 16; 8 for RSAI_FP64) */
-    int32_t global_bin_ctas;      /* CTAs of the global bin, 0 = one per column that reaches it, <= SMs */
+    int32_t global_bin_ctas;      /* CTAs of the global bin, 0 = one per column that reaches it, <= SMs;
+                                     the bin's global-memory workspace (one slab per CTA) is resized to
+                                     match */
     int32_t half_bin;             /* 1: columns start in the half-warp bin (two columns per warp, |I| <= 48,
                                      |J| <= 16) and move on to the warp bin when they outgrow it; 0: they start
                                      in the warp bin.  Default 1 for RSAI_FP64, 0 for RSAI_FP32_REFINE. */

@@ -1157,8 +1157,9 @@ rsai_status rsai_set_tuning(rsai_handle *h, const rsai_tuning *t) {
     if (plan_w2(h, fp32) != RSAI_OK) return RSAI_ERR_CUDA;
     if (t->global_bin_ctas > 0) {
         const int want = std::min(t->global_bin_ctas, h->sms);
-        if (want > h->grid_g) {
-            // the larger slab first, so that a failed allocation leaves the old one in place
+        if (want > h->grid_g || (h->gwork && want < h->grid_g)) {
+            // the slab follows the CTA count (one workspace per CTA); the new one
+            // first, so that a failed allocation leaves the old one in place
             char *slab = nullptr;
             int rc = dalloc(h, &slab, h->gstride * (size_t)want, st);
             if (rc != RSAI_OK) return (rsai_status)rc;

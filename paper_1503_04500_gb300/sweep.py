@@ -45,8 +45,10 @@ def _ints(s: str):
 
 
 def run(workload="convdiff2d", size=20, seed=1503, eps=(0.3,), c=(3,), lmax=(10,), drop="fixed", tol=1e-3,
-        precision="fp64", side="right", rebuilds=5, solve=True, init="identity", select="rsai", A=None):
-    """Yield one result dict per (eps, c, l_max) setting."""
+        precision="fp64", side="right", rebuilds=5, solve=True, init="identity", select="rsai", A=None,
+        global_ctas=0):
+    """Yield one result dict per (eps, c, l_max) setting.  `global_ctas` > 0:
+    the rebuilds run the global bin on that many CTAs (and workspace slabs)."""
     import torch
 
     A = A if A is not None else _workload(workload, size, seed)
@@ -60,6 +62,8 @@ def run(workload="convdiff2d", size=20, seed=1503, eps=(0.3,), c=(3,), lmax=(10,
         torch.cuda.synchronize()
         first_s = time.perf_counter() - t0
         right = h.right if side == "left" else h
+        if global_ctas > 0:
+            right.set_tuning(global_bin_ctas=global_ctas)
         times = []
         for _ in range(rebuilds):
             e0 = torch.cuda.Event(enable_timing=True)
@@ -184,6 +188,8 @@ def main(argv=None):
                     help="new indices: dominant rows (Algorithm 1) or SPAI's most profitable (Eqs. 2.5-2.7)")
     ap.add_argument("--compare-spai", action="store_true",
                     help="instead of a sweep: RSAI(tol) against SPAI with Section 5.2's settings")
+    ap.add_argument("--global-ctas", type=int, default=0,
+                    help="CTAs (and workspace slabs) of the global bin in the rebuilds, 0 = one per SM")
     ap.add_argument("--batch", type=int, default=0,
                     help="instead of a sweep: a batch of this many random members (n up to --size) in one build")
     a = ap.parse_args(argv)
@@ -195,7 +201,7 @@ def main(argv=None):
                                    a.drop, a.tol, max(a.rebuilds, 1))), flush=True)
         return
     for row in run(a.workload, a.size, a.seed, _floats(a.eps), _ints(a.c), _ints(a.lmax), a.drop, a.tol,
-                   a.precision, a.side, a.rebuilds, a.solve, a.init, a.select):
+                   a.precision, a.side, a.rebuilds, a.solve, a.init, a.select, None, a.global_ctas):
         print(json.dumps(row), flush=True)
 
 
