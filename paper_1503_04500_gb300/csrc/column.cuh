@@ -43,6 +43,9 @@ struct Caps {
     int spai;         // SPAI selection: a score per candidate column (scap of them)
 };
 
+// Columns of one compact-WY panel (global-memory bins)
+constexpr int kPanel = 16;
+
 template <typename T> struct Work {
     T *B, *vhead, *tau, *rhs;
     double *m, *r, *z, *wv;
@@ -52,6 +55,12 @@ template <typename T> struct Work {
     double *sc;        // SPAI: the score s_j of each candidate (Caps::spai)
     int32_t *Ip, *Jp;  // factor position of each sorted I / J entry (Caps::append)
     T *qte;            // Q^T e_k(I) of the kept factor, factor row order (Caps::append)
+    // Global-memory bins (Caps::stage_bytes > 0): the reflectors as factored,
+    // in panels: pnb[j0] reflectors start at j0, and column j of the panel's
+    // compact-WY T (H_j0 ... H_j0+nb-1 = I - V T V^T) is Tst[j * kPanel + s],
+    // s <= j - j0.  A reflector factored on its own is a panel of one, T = tau.
+    T *Tst;
+    int32_t *pnb;
     char *stage = nullptr;  // panel staging area (shared memory), not part of the carved workspace
 
     __host__ __device__ static size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -78,6 +87,10 @@ template <typename T> struct Work {
             b += align16(sizeof(int32_t) * (size_t)c.qcap);
             b += align16(sizeof(int32_t) * (size_t)c.pcap);
             b += align16(sizeof(T) * (size_t)(c.qcap + 1));
+        }
+        if (c.stage_bytes > 0) {
+            b += align16(sizeof(T) * (size_t)c.pcap * kPanel);
+            b += align16(sizeof(int32_t) * (size_t)c.pcap);
         }
         return b;
     }
@@ -113,6 +126,12 @@ template <typename T> struct Work {
             Ip = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.qcap);
             Jp = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.pcap);
             qte = (T *)(base + o); o += align16(sizeof(T) * (size_t)(c.qcap + 1));
+        }
+        Tst = nullptr;
+        pnb = nullptr;
+        if (c.stage_bytes > 0) {
+            Tst = (T *)(base + o); o += align16(sizeof(T) * (size_t)c.pcap * kPanel);
+            pnb = (int32_t *)(base + o); o += align16(sizeof(int32_t) * (size_t)c.pcap);
         }
     }
 };
@@ -247,8 +266,6 @@ __device__ __noinline__ int qr_factor_team(Team team, T *B, int q, int p, T *rhs
     return rank_flag;
 }
 
-constexpr int kPanel = 16;
-
 // Compact-WY pieces shared by the panel factorization and the QR update.
 // V: nb explicit reflectors (zeros above the diagonal, heads on it) of
 // length qq in shared memory, ld qq; taus: their 2 / v^T v.
@@ -288,15 +305,15 @@ __device__ __forceinline__ void wy_form_T(const Team &team, const T *V, int qq, 
 
 // Columns c in [c_lo, c_hi] of B (ld q; c == p stands for rhs), rows
 // j0..j0+qq-1: C <- C - V (T^T (V^T C)).  Each warp takes kCols columns at a
-// time so that every reflector value read from shared memory serves kCols
-// columns.  Ends with a team synchronisation.
+// time (four in FP32, two in FP64) so that every reflector value read from
+// shared memory serves kCols columns.  Ends with a team synchronisation.
 template <class Team, typename T>
 __device__ __forceinline__ void wy_apply(const Team &team, const T *V, int qq, int nb, const T *tm, T *B, int q,
                                          int p, T *rhs, int j0, int c_lo, int c_hi) {
     const int me = team.rank();
     const int lane = me & 31, wid = me >> 5;
     constexpr int NW = (Team::SIZE + 31) / 32;
-    constexpr int kCols = 4;
+    constexpr int kCols = sizeof(T) == 8 ? 2 : 4;  // W of kCols x kPanel values stays in registers
     for (int c0 = c_lo + wid * kCols; c0 <= c_hi; c0 += NW * kCols) {
         T *tc[kCols];
 #pragma unroll
@@ -378,6 +395,249 @@ __device__ __forceinline__ void wy_apply(const Team &team, const T *V, int qq, i
     team.sync();
 }
 
+// Head of the panel staging area (global-memory bins), in elements of T: the
+// panel's T (kPanel x kPanel), the CTA reduction slots (kPanel per warp) and
+// two kPanel-vectors of results; the staged panel V follows.
+template <class Team> constexpr int kStageHead = kPanel * kPanel + (Team::SIZE / 32 + 2) * kPanel;
+
+// Sum of kPanel values over the 32 lanes of a warp by halving exchanges (a
+// lane keeps the half of its vector that its partner sends back summed): 16
+// shuffles instead of 16 x 5.  Lanes 2e and 2e+1 end up holding the sum of
+// entry rs_entry(lane) in v[0].
+__device__ __forceinline__ int rs_entry(int lane) {
+    return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+template <typename T> __device__ __forceinline__ T warp_reduce_scatter16(T (&v)[kPanel], int lane) {
+    static_assert(kPanel == 16, "the exchange pattern below is written for 16 values");
+#pragma unroll
+    for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const T send = up ? v[i] : v[i + h];
+            const T keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// out[0..kPanel) = the sums of v[0..kPanel) over the CTA, visible to every
+// thread on return (two synchronisations; the warps' partial sums go through
+// red, kPanel per warp, and are added in warp order).
+template <class Team, typename T>
+__device__ __forceinline__ void team_sum16(const Team &team, T (&v)[kPanel], T *red, T *out) {
+    constexpr int NW = Team::SIZE / 32;
+    const int me = team.rank(), lane = me & 31;
+    const T sv = warp_reduce_scatter16(v, lane);
+    if ((lane & 1) == 0) red[(me >> 5) * kPanel + rs_entry(lane)] = sv;
+    team.sync();
+    if (me < kPanel) {
+        T a = red[me];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) a += red[w * kPanel + me];
+        out[me] = a;
+    }
+    team.sync();
+}
+
+// Asynchronous element copies global -> shared (cp.async, 4 or 8 bytes: no
+// alignment beyond the element's own); cp_async_wait waits for the calling
+// thread's copies.
+template <typename T> __device__ __forceinline__ void cp_async_elem(T *smem_dst, const T *gmem_src) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem_src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// rhs[0..p) <- R^{-1} rhs[0..p) for a CTA team, in blocks of kBS rows from
+// the bottom: one warp solves the block's triangle (lane l holds row b0 + l
+// and loads its row of the block into registers first), then every thread
+// subtracts the block's part from the rows above.  Each row receives its
+// terms in the same order (descending column) as the one-row-at-a-time
+// version, so the results are identical.
+template <class Team, typename T>
+__device__ void back_substitute_blocked(const Team &team, const T *B, int q, int p, T *rhs, T small) {
+    constexpr int kBS = sizeof(T) == 8 ? 16 : 32;
+    const int me = team.rank();
+    for (int b1 = p; b1 > 0;) {
+        const int b0 = max(0, b1 - kBS);
+        const int nbk = b1 - b0;
+        if (me < 32) {
+            const int i = b0 + me;
+            const bool row = me < nbk;
+            T rv[kBS];
+#pragma unroll
+            for (int u = 0; u < kBS; ++u) rv[u] = (row && u < nbk) ? B[(int64_t)(b0 + u) * q + i] : T(0);
+            const T dd = row ? B[(int64_t)i * q + i] : T(1);
+            T xi = row ? rhs[i] : T(0);
+#pragma unroll
+            for (int u = kBS - 1; u >= 0; --u) {
+                if (u < nbk) {
+                    const T rr = __shfl_sync(0xffffffffu, xi, u);
+                    const T d = __shfl_sync(0xffffffffu, dd, u);
+                    const T xr = (fabs(d) <= small) ? T(0) : rr / d;
+                    if (me == u) xi = xr;
+                    else if (me < u) xi -= rv[u] * xr;
+                }
+            }
+            if (row) rhs[i] = xi;
+        }
+        team.sync();
+        for (int c = me; c < b0; c += Team::SIZE) {
+            T bv[kBS];
+#pragma unroll
+            for (int u = 0; u < kBS; ++u) bv[u] = (u < nbk) ? B[(int64_t)(b0 + u) * q + c] : T(0);
+            T a = rhs[c];
+#pragma unroll
+            for (int u = kBS - 1; u >= 0; --u)
+                if (u < nbk) a -= bv[u] * rhs[b0 + u];
+            rhs[c] = a;
+        }
+        team.sync();
+        b1 = b0;
+    }
+}
+
+// Householder QR of the staged panel V (rows 0..qq-1, nb <= kPanel columns,
+// ld qq, shared memory) with the T of its compact-WY form built alongside.
+// Step t makes one pass over rows r >= t for x.x (x = column t), c.x for the
+// trailing panel columns c and v_s.x for the earlier reflectors s, and one
+// CTA reduction of the kPanel sums.  Since v_t differs from x only in its head
+// (v0 instead of x0), v_t.c = c.x + (v0 - x0) c_t and Y(s,t) = v_s.v_t =
+// v_s.x + (v0 - x0) v_s(t); then T(t,t) = tau_t and
+// T(s,t) = -tau_t sum_{s <= s2 < t} T(s,s2) Y(s2,t) (tm[s * kPanel + t]).
+// Leaves R on and above the diagonal, the reflector tails below it, and
+// vhead[t] = v0, taus[t] = 2 / v^T v.
+template <class Team, typename T>
+__device__ __forceinline__ void panel_factor_fused(const Team &team, T *V, int qq, int nb, T *vhead, T *taus, T *tm,
+                                                   T *red, T *out, T *out2, T small, int &rank_flag) {
+    const int me = team.rank();
+    for (int t = 0; t < nb; ++t) {
+        T *x = V + (int64_t)t * qq;
+        T acc[kPanel];
+#pragma unroll
+        for (int u = 0; u < kPanel; ++u) acc[u] = T(0);
+        for (int r = t + me; r < qq; r += Team::SIZE) {
+            const T xr = x[r];
+#pragma unroll
+            for (int u = 0; u < kPanel; ++u)
+                if (u < nb) acc[u] += V[(int64_t)u * qq + r] * xr;
+        }
+        team_sum16(team, acc, red, out);
+        const T sigma = out[t];
+        const T x0 = x[t];
+        const T nrm = sqrt(sigma);
+        const T alpha = (x0 >= T(0)) ? -nrm : nrm;
+        const T v0 = x0 - alpha;
+        const T vtv = sigma - x0 * x0 + v0 * v0;
+        const T two_over = (vtv > T(0)) ? T(2) / vtv : T(0);
+        if (me < nb && me != t) {
+            const T d = out[me] + (v0 - x0) * V[(int64_t)me * qq + t];
+            out2[me] = (me > t) ? d * two_over : d;  // f_c for c > t, Y(s,t) for s < t
+        }
+        team.sync();
+        if (two_over > T(0)) {
+            for (int r = t + me; r < qq; r += Team::SIZE) {
+                const T vr = (r == t) ? v0 : x[r];
+#pragma unroll
+                for (int u = 0; u < kPanel; ++u)
+                    if (u > t && u < nb) V[(int64_t)u * qq + r] -= out2[u] * vr;
+            }
+        }
+        if (me < t) {
+            T a = 0;
+            for (int s2 = me; s2 < t; ++s2) a += tm[me * kPanel + s2] * out2[s2];
+            tm[me * kPanel + t] = -two_over * a;
+        } else if (me == t) {
+            tm[t * kPanel + t] = two_over;
+        }
+        team.sync();
+        if (me == 0) {
+            x[t] = alpha;
+            vhead[t] = v0;
+            taus[t] = two_over;
+        }
+        rank_flag |= (fabs(alpha) <= small) ? 1 : 0;
+    }
+    team.sync();
+}
+
+// rhs <- Q^T rhs with the reflectors in the panels they were factored in
+// (pnb, Tst): per panel w = V^T rhs (one CTA reduction), y = T^T w, and
+// rhs <- rhs - V y, with V = the explicit reflectors (vhead on the diagonal,
+// the tails of B below it).  A panel whose V fits the staging area is copied
+// there first (cp.async) and both passes read shared memory.
+template <class Team, typename T>
+__device__ __noinline__ void apply_qt_panels(Team team, const T *B, int q, int p, T *rhs, const T *vhead,
+                                             const T *Tst, const int32_t *pnb, T *stage, int stage_bytes) {
+    constexpr int NW = Team::SIZE / 32;
+    const int me = team.rank();
+    T *red = stage + kPanel * kPanel, *out = red + NW * kPanel, *out2 = out + kPanel;
+    T *V = stage + kStageHead<Team>;
+    const int64_t velems = (int64_t)stage_bytes / (int64_t)sizeof(T) - kStageHead<Team>;
+    for (int j0 = 0; j0 < p;) {
+        const int nb = pnb[j0];
+        const int qq = q - j0;
+        const bool staged = nb > 1 && (int64_t)nb * qq <= velems;
+        if (staged) {
+            for (int t = 0; t < nb; ++t) {
+                const T *src = B + (int64_t)(j0 + t) * q + j0;
+                T *dst = V + (int64_t)t * qq;
+                for (int r = me; r < qq; r += Team::SIZE) {
+                    if (r > t) cp_async_elem(dst + r, src + r);
+                    else dst[r] = (r == t) ? vhead[j0 + t] : T(0);
+                }
+            }
+            cp_async_wait();
+            team.sync();
+        }
+        T acc[kPanel];
+#pragma unroll
+        for (int u = 0; u < kPanel; ++u) acc[u] = T(0);
+        for (int i = j0 + me; i < q; i += Team::SIZE) {
+            const T x = rhs[i];
+            const int r = i - j0;
+#pragma unroll
+            for (int u = 0; u < kPanel; ++u) {
+                if (u < nb) {
+                    const int j = j0 + u;
+                    const T v = staged ? V[(int64_t)u * qq + r]
+                                       : ((i > j) ? B[(int64_t)j * q + i] : ((i == j) ? vhead[j] : T(0)));
+                    acc[u] += v * x;
+                }
+            }
+        }
+        team_sum16(team, acc, red, out);
+        if (me < nb) {
+            T y = 0;
+            for (int s2 = 0; s2 <= me; ++s2) y += Tst[(int64_t)(j0 + me) * kPanel + s2] * out[s2];
+            out2[me] = y;
+        }
+        team.sync();
+        for (int i = j0 + me; i < q; i += Team::SIZE) {
+            T a = rhs[i];
+            const int r = i - j0;
+#pragma unroll
+            for (int u = 0; u < kPanel; ++u) {
+                if (u < nb) {
+                    const int j = j0 + u;
+                    const T v = staged ? V[(int64_t)u * qq + r]
+                                       : ((i > j) ? B[(int64_t)j * q + i] : ((i == j) ? vhead[j] : T(0)));
+                    a -= v * out2[u];
+                }
+            }
+            rhs[i] = a;
+        }
+        team.sync();
+        j0 += nb;
+    }
+}
+
 // Blocked Householder QR (compact WY) for the bins whose workspace is in
 // global memory.  Panels of nb <= kPanel columns (nb chosen so that rows j0..q
 // of the panel fit the shared-memory staging area) are copied to shared
@@ -394,14 +654,15 @@ __device__ __forceinline__ void wy_apply(const Team &team, const T *V, int qq, i
 // leaves Q^T rhs in rhs.
 template <class Team, typename T>
 __device__ __noinline__ int qr_solve_staged(Team team, T *B, int q, int p, T *rhs, T *vhead, T *taus, T small,
-                                            T *stage, int stage_bytes,
+                                            T *stage, int stage_bytes, T *Tst, int32_t *pnb,
                                             int j_start = 0, bool backsub = true) {
     const int me = team.rank();
-    const int lane = me & 31, wid = me >> 5;
-    constexpr int NW = (Team::SIZE + 31) / 32;
-    T *tm = stage;                     // kPanel x kPanel
-    T *V = stage + kPanel * kPanel;    // panel, ld = q - j0
-    const int64_t velems = (int64_t)stage_bytes / (int64_t)sizeof(T) - kPanel * kPanel;
+    constexpr int NW = Team::SIZE / 32;
+    T *tm = stage;                                  // kPanel x kPanel
+    T *red = stage + kPanel * kPanel;               // reduction slots
+    T *out = red + NW * kPanel, *out2 = out + kPanel;
+    T *V = stage + kStageHead<Team>;                // panel, ld = q - j0
+    const int64_t velems = (int64_t)stage_bytes / (int64_t)sizeof(T) - kStageHead<Team>;
     int rank_flag = 0;
     int j0 = j_start;
     while (j0 < p) {
@@ -410,48 +671,23 @@ __device__ __noinline__ int qr_solve_staged(Team team, T *B, int q, int p, T *rh
         nb = min(nb, p - j0);
         if (nb < 4) {
             householder_step(team, B, q, p, rhs, vhead, taus, j0, j0 + 1, small, rank_flag);
+            if (me == 0) {
+                pnb[j0] = 1;
+                Tst[(int64_t)j0 * kPanel] = taus[j0];
+            }
             ++j0;
             continue;
         }
-        // 1. stage rows j0..q-1 of the panel columns
-        for (int idx = me; idx < nb * qq; idx += Team::SIZE) {
-            const int t = idx / qq, r = idx - t * qq;
-            V[idx] = B[(int64_t)(j0 + t) * q + j0 + r];
-        }
-        team.sync();
-        // 2. factor the panel in shared memory (local rows r = i - j0)
+        // 1. stage rows j0..q-1 of the panel columns (asynchronous copies)
         for (int t = 0; t < nb; ++t) {
-            T *col = V + (int64_t)t * qq;
-            T part = 0;
-            for (int r = t + me; r < qq; r += Team::SIZE) part += col[r] * col[r];
-            const T sigma = team.sum(part);
-            const T x0 = col[t];
-            const T nrm = sqrt(sigma);
-            const T alpha = (x0 >= T(0)) ? -nrm : nrm;
-            const T v0 = x0 - alpha;
-            const T vtv = sigma - x0 * x0 + v0 * v0;
-            const T two_over = (vtv > T(0)) ? T(2) / vtv : T(0);
-            if (two_over > T(0)) {
-                for (int c = t + 1 + wid; c < nb; c += NW) {
-                    T *cc = V + (int64_t)c * qq;
-                    T d = 0;
-                    for (int r = t + lane; r < qq; r += 32) d += ((r == t) ? v0 : col[r]) * cc[r];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-                    const T f = d * two_over;
-                    for (int r = t + lane; r < qq; r += 32) cc[r] -= f * ((r == t) ? v0 : col[r]);
-                }
-            }
-            team.sync();
-            if (me == 0) {
-                col[t] = alpha;
-                vhead[j0 + t] = v0;
-                taus[j0 + t] = two_over;
-            }
-            rank_flag |= (fabs(alpha) <= small) ? 1 : 0;
-            team.sync();
+            const T *src = B + (int64_t)(j0 + t) * q + j0;
+            for (int r = me; r < qq; r += Team::SIZE) cp_async_elem(V + (int64_t)t * qq + r, src + r);
         }
-        // 3. panel back to B (R entries and reflector tails), 4. explicit V
+        cp_async_wait();
+        team.sync();
+        // 2. factor the panel in shared memory (local rows r = i - j0), T alongside
+        panel_factor_fused(team, V, qq, nb, vhead + j0, taus + j0, tm, red, out, out2, small, rank_flag);
+        // 3. panel back to B (R entries and reflector tails), 4. explicit V, T kept
         for (int idx = me; idx < nb * qq; idx += Team::SIZE) {
             const int t = idx / qq, r = idx - t * qq;
             B[(int64_t)(j0 + t) * q + j0 + r] = V[idx];
@@ -462,14 +698,17 @@ __device__ __noinline__ int qr_solve_staged(Team team, T *B, int q, int p, T *rh
             if (r < t) V[idx] = T(0);
             else if (r == t) V[idx] = vhead[j0 + t];
         }
-        for (int e = me; e < kPanel * kPanel; e += Team::SIZE) tm[e] = T(0);
+        for (int e = me; e < nb * kPanel; e += Team::SIZE) {
+            const int t = e / kPanel, s2 = e - t * kPanel;
+            Tst[(int64_t)(j0 + t) * kPanel + s2] = (s2 <= t) ? tm[s2 * kPanel + t] : T(0);
+        }
+        if (me == 0) pnb[j0] = nb;
         team.sync();
-        // 5. T, 6. trailing columns and rhs, rows j0..q-1
-        wy_form_T(team, V, qq, nb, taus + j0, tm);
+        // 5. trailing columns and rhs, rows j0..q-1
         wy_apply(team, V, qq, nb, tm, B, q, p, rhs, j0, j0 + nb, p);
         j0 += nb;
     }
-    if (backsub) back_substitute_team(team, B, q, p, rhs, small);
+    if (backsub) back_substitute_blocked(team, B, q, p, rhs, small);
     return rank_flag;
 }
 
@@ -492,54 +731,65 @@ __device__ __noinline__ void apply_qt_team(Team team, const T *B, int q, int p, 
         }
         team.sync();
     }
-    back_substitute_team(team, B, q, p, rhs, small);
+    if constexpr (is_lane_team<Team>::value) back_substitute_team(team, B, q, p, rhs, small);
+    else back_substitute_blocked(team, B, q, p, rhs, small);
 }
 
 // The QR update of Section 3, first half: the reflectors 0..p0-1 of a
 // finished factor (built on q0 rows; every row below is zero in them) applied
-// to the appended columns p0..p-1 of B (ld q), rows j..q0-1.  With a staging
-// area, panels of up to kPanel old reflectors are copied to shared memory as
-// explicit V and applied in compact-WY form; otherwise (or when a panel does
-// not fit four reflectors) one reflector per pass, one warp per column.
+// to the appended columns p0..p-1 of B (ld q), rows j..q0-1.  In the
+// global-memory bins (pnb != nullptr) the reflectors go panel by panel as
+// they were factored: a panel whose explicit V fits the staging area is
+// applied in compact-WY form with its stored T.  Otherwise (and in the
+// shared-memory bins) one reflector per pass, one warp per column.
 template <class Team, typename T>
 __device__ __noinline__ void qr_update_apply(Team team, T *B, int q, int p, int q0, int p0, const T *vhead,
-                                             const T *taus, T *stage, int stage_bytes) {
+                                             const T *taus, T *stage, int stage_bytes, const T *Tst,
+                                             const int32_t *pnb) {
     const int me = team.rank();
     const int lane = me & 31, wid = me >> 5;
     constexpr int NW = (Team::SIZE + 31) / 32;
     T *tm = stage;
-    T *V = stage + kPanel * kPanel;
-    const int64_t velems = stage_bytes > 0 ? (int64_t)stage_bytes / (int64_t)sizeof(T) - kPanel * kPanel : 0;
+    T *V = stage + kStageHead<Team>;
+    const int64_t velems = stage_bytes > 0 ? (int64_t)stage_bytes / (int64_t)sizeof(T) - kStageHead<Team> : 0;
     int j0 = 0;
     while (j0 < p0) {
         const int qq = q0 - j0;
-        int nb = (int)min((int64_t)kPanel, velems / (int64_t)max(qq, 1));
-        nb = min(nb, p0 - j0);
-        if (nb < 4) {
-            const T *col = B + (int64_t)j0 * q;
-            const T v0 = vhead[j0], two_over = taus[j0];
-            if (two_over > T(0)) {
-                for (int c = p0 + wid; c < p; c += NW) {
-                    T *t = B + (int64_t)c * q;
-                    T d = 0;
-                    for (int i = j0 + lane; i < q0; i += 32) d += ((i == j0) ? v0 : col[i]) * t[i];
+        const int nb = pnb ? pnb[j0] : 1;
+        if (nb < 4 || (int64_t)nb * qq > velems) {
+            for (int j = j0; j < j0 + nb; ++j) {
+                const T *col = B + (int64_t)j * q;
+                const T v0 = vhead[j], two_over = taus[j];
+                if (two_over > T(0)) {
+                    for (int c = p0 + wid; c < p; c += NW) {
+                        T *t = B + (int64_t)c * q;
+                        T d = 0;
+                        for (int i = j + lane; i < q0; i += 32) d += ((i == j) ? v0 : col[i]) * t[i];
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-                    const T f = d * two_over;
-                    for (int i = j0 + lane; i < q0; i += 32) t[i] -= f * ((i == j0) ? v0 : col[i]);
+                        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                        const T f = d * two_over;
+                        for (int i = j + lane; i < q0; i += 32) t[i] -= f * ((i == j) ? v0 : col[i]);
+                    }
                 }
+                team.sync();
             }
-            team.sync();
-            ++j0;
+            j0 += nb;
             continue;
         }
-        for (int idx = me; idx < nb * qq; idx += Team::SIZE) {
-            const int t = idx / qq, r = idx - t * qq;
-            V[idx] = (r < t) ? T(0) : ((r == t) ? vhead[j0 + t] : B[(int64_t)(j0 + t) * q + j0 + r]);
+        for (int t = 0; t < nb; ++t) {
+            const T *src = B + (int64_t)(j0 + t) * q + j0;
+            T *dst = V + (int64_t)t * qq;
+            for (int r = me; r < qq; r += Team::SIZE) {
+                if (r > t) cp_async_elem(dst + r, src + r);
+                else dst[r] = (r == t) ? vhead[j0 + t] : T(0);
+            }
         }
-        for (int e = me; e < kPanel * kPanel; e += Team::SIZE) tm[e] = T(0);
+        cp_async_wait();
+        for (int e = me; e < kPanel * kPanel; e += Team::SIZE) {
+            const int s2 = e / kPanel, t = e - s2 * kPanel;
+            tm[e] = (t < nb && s2 <= t) ? Tst[(int64_t)(j0 + t) * kPanel + s2] : T(0);
+        }
         team.sync();
-        wy_form_T(team, V, qq, nb, taus + j0, tm);
         wy_apply(team, V, qq, nb, tm, B, q, p, (T *)nullptr, j0, p0, p - 1);
         j0 += nb;
     }
@@ -821,10 +1071,13 @@ template <class Team, typename T> struct Column {
             const bool keep = cap.append != 0;  // keep Q^T e_k for later updates
             if (cap.stage_bytes > 0 && p >= 2 * kPanel)
                 rank_flag = qr_solve_staged<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.tau, small, (T *)w.stage,
-                                                     cap.stage_bytes, 0, !keep);
-            else
-                rank_flag = keep ? qr_factor_team<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.tau, small, 0)
-                                 : qr_solve_team<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.tau, small);
+                                                     cap.stage_bytes, w.Tst, w.pnb, 0, !keep);
+            else if (keep) {
+                rank_flag = qr_factor_team<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.tau, small, 0);
+                single_panels(0);
+            } else {
+                rank_flag = qr_solve_team<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.tau, small);
+            }
             if (keep) {
                 // a factor from scratch: factor order = sorted order
                 const int me = team.rank();
@@ -834,12 +1087,22 @@ template <class Team, typename T> struct Column {
                 }
                 for (int c = me; c < p; c += Team::SIZE) w.Jp[c] = c;
                 team.sync();
-                back_substitute_team(team, w.B, q, p, w.rhs, small);
+                back_substitute_blocked(team, w.B, q, p, w.rhs, small);
                 fact_valid = true;
             }
             return;
         }
         rank_flag = qr_solve_team<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.tau, small);
+    }
+
+    // Reflectors j0..p-1 factored one at a time: panels of one (global-memory bins)
+    __device__ void single_panels(int j0) {
+        if (w.pnb == nullptr) return;
+        for (int j = j0 + team.rank(); j < p; j += Team::SIZE) {
+            w.pnb[j] = 1;
+            w.Tst[(int64_t)j * kPanel] = w.tau[j];
+        }
+        team.sync();
     }
 
     // factor row of sorted I position i / factor column of sorted J position c
@@ -857,6 +1120,14 @@ template <class Team, typename T> struct Column {
         if constexpr (is_lane_team<Team>::value) {
             if (p > 2 && p <= cap.small_p && q <= Team::SIZE * kRegRows<Team>) {
                 lanes_apply_qt_small<Team::SIZE, kRegRows<Team>>(w.B, q, p, w.rhs, w.vhead, w.tau, small);
+                return;
+            }
+        }
+        if constexpr (!is_lane_team<Team>::value) {
+            if (w.pnb != nullptr) {
+                apply_qt_panels<Team, T>(team, w.B, q, p, w.rhs, w.vhead, w.Tst, w.pnb, (T *)w.stage,
+                                         cap.stage_bytes);
+                back_substitute_blocked(team, w.B, q, p, w.rhs, small);
                 return;
             }
         }
@@ -1106,18 +1377,21 @@ template <class Team, typename T> struct Column {
             if (ik < q && w.I[ik] == k && w.Ip[ik] >= qo) w.qte[w.Ip[ik]] = T(1);
         }
         team.sync();
-        qr_update_apply<Team, T>(team, w.B, q, p, qo, po, w.vhead, w.tau, (T *)w.stage, cap.stage_bytes);
-        if (cap.stage_bytes > 0 && p >= 2 * kPanel)
+        qr_update_apply<Team, T>(team, w.B, q, p, qo, po, w.vhead, w.tau, (T *)w.stage, cap.stage_bytes, w.Tst,
+                                 w.pnb);
+        if (cap.stage_bytes > 0 && p >= 2 * kPanel) {
             qr_solve_staged<Team, T>(team, w.B, q, p, w.qte, w.vhead, w.tau, small, (T *)w.stage, cap.stage_bytes,
-                                     po, false);
-        else
+                                     w.Tst, w.pnb, po, false);
+        } else {
             qr_factor_team<Team, T>(team, w.B, q, p, w.qte, w.vhead, w.tau, small, po);
+            single_panels(po);
+        }
         int rf = 0;
         for (int j = me; j < p; j += Team::SIZE) rf |= (fabs(w.B[(int64_t)j * q + j]) <= small) ? 1 : 0;
         rank_flag = team.sum(rf) > 0 ? 1 : 0;
         for (int j = me; j < p; j += Team::SIZE) w.rhs[j] = w.qte[j];
         team.sync();
-        back_substitute_team(team, w.B, q, p, w.rhs, small);
+        back_substitute_blocked(team, w.B, q, p, w.rhs, small);
         for (int c = me; c < p; c += Team::SIZE) w.m[c] = (double)w.rhs[w.Jp[c]];
         team.sync();
         fact_valid = true;
@@ -1412,7 +1686,8 @@ template <class Team, typename T> struct Column {
             if (me == 0) w.rhs[i] = yi;
             team.sync();
         }
-        back_substitute_team(team, w.B, q, p, w.rhs, small);
+        if constexpr (is_lane_team<Team>::value) back_substitute_team(team, w.B, q, p, w.rhs, small);
+        else back_substitute_blocked(team, w.B, q, p, w.rhs, small);
     }
 
     // Refit: solve on the loaded pattern, then the residual.  Returns false on
