@@ -306,7 +306,10 @@ __device__ __forceinline__ void wy_form_T(const Team &team, const T *V, int qq, 
 // Columns c in [c_lo, c_hi] of B (ld q; c == p stands for rhs), rows
 // j0..j0+qq-1: C <- C - V (T^T (V^T C)).  Each warp takes kCols columns at a
 // time (four in FP32, two in FP64) so that every reflector value read from
-// shared memory serves kCols columns.  Ends with a team synchronisation.
+// shared memory serves kCols columns, kRows rows per lane and pass.  A pass
+// over kRows full rows of a full panel takes a path without per-element bounds
+// tests (a warp's missing columns read its first column again and store
+// nothing).  Ends with a team synchronisation.
 template <class Team, typename T>
 __device__ __forceinline__ void wy_apply(const Team &team, const T *V, int qq, int nb, const T *tm, T *B, int q,
                                          int p, T *rhs, int j0, int c_lo, int c_hi) {
@@ -314,22 +317,47 @@ __device__ __forceinline__ void wy_apply(const Team &team, const T *V, int qq, i
     const int lane = me & 31, wid = me >> 5;
     constexpr int NW = (Team::SIZE + 31) / 32;
     constexpr int kCols = sizeof(T) == 8 ? 2 : 4;  // W of kCols x kPanel values stays in registers
+    constexpr int kRows = 4;
+    const bool full_panel = nb == kPanel;
     for (int c0 = c_lo + wid * kCols; c0 <= c_hi; c0 += NW * kCols) {
         T *tc[kCols];
+        bool has[kCols];
 #pragma unroll
         for (int x = 0; x < kCols; ++x) {
             const int c = c0 + x;
-            tc[x] = (c > c_hi) ? nullptr : ((c < p) ? B + (int64_t)c * q + j0 : rhs + j0);
+            has[x] = c <= c_hi;
+            tc[x] = !has[x] ? nullptr : ((c < p) ? B + (int64_t)c * q + j0 : rhs + j0);
         }
+        T *tf[kCols];  // the fast path's columns: a missing one reads column c0
+#pragma unroll
+        for (int x = 0; x < kCols; ++x) tf[x] = has[x] ? tc[x] : tc[0];
+        const bool all_cols = full_panel;  // every present column on the fast path
         T wv[kCols][kPanel];
 #pragma unroll
         for (int x = 0; x < kCols; ++x)
 #pragma unroll
             for (int u = 0; u < kPanel; ++u) wv[x][u] = T(0);
-        // kRows rows per pass (r, r + 32, ...), their loads issued before any use
-        constexpr int kRows = 4;
+        // W = V^T C; kRows rows per pass (r, r + 32, ...), their loads issued before any use
         for (int r = lane; r < qq; r += 32 * kRows) {
             T cr[kRows][kCols];
+            if (all_cols && r + 32 * (kRows - 1) < qq) {
+#pragma unroll
+                for (int y = 0; y < kRows; ++y)
+#pragma unroll
+                    for (int x = 0; x < kCols; ++x) cr[y][x] = tf[x][r + 32 * y];
+#pragma unroll
+                for (int u = 0; u < kPanel; ++u) {
+                    const T *vu = V + (int64_t)u * qq + r;
+                    T v[kRows];
+#pragma unroll
+                    for (int y = 0; y < kRows; ++y) v[y] = vu[32 * y];
+#pragma unroll
+                    for (int x = 0; x < kCols; ++x)
+#pragma unroll
+                        for (int y = 0; y < kRows; ++y) wv[x][u] += v[y] * cr[y][x];
+                }
+                continue;
+            }
 #pragma unroll
             for (int y = 0; y < kRows; ++y)
 #pragma unroll
@@ -341,12 +369,9 @@ __device__ __forceinline__ void wy_apply(const Team &team, const T *V, int qq, i
 #pragma unroll
                     for (int y = 0; y < kRows; ++y) v[y] = (r + 32 * y < qq) ? V[(int64_t)u * qq + r + 32 * y] : T(0);
 #pragma unroll
-                    for (int x = 0; x < kCols; ++x) {
-                        T sacc = 0;
+                    for (int x = 0; x < kCols; ++x)
 #pragma unroll
-                        for (int y = 0; y < kRows; ++y) sacc += v[y] * cr[y][x];
-                        wv[x][u] += sacc;
-                    }
+                        for (int y = 0; y < kRows; ++y) wv[x][u] += v[y] * cr[y][x];
                 }
             }
         }
@@ -370,6 +395,28 @@ __device__ __forceinline__ void wy_apply(const Team &team, const T *V, int qq, i
         }
         for (int r = lane; r < qq; r += 32 * kRows) {
             T acc[kRows][kCols];
+            if (all_cols && r + 32 * (kRows - 1) < qq) {
+#pragma unroll
+                for (int y = 0; y < kRows; ++y)
+#pragma unroll
+                    for (int x = 0; x < kCols; ++x) acc[y][x] = tf[x][r + 32 * y];
+#pragma unroll
+                for (int u = 0; u < kPanel; ++u) {
+                    const T *vu = V + (int64_t)u * qq + r;
+#pragma unroll
+                    for (int y = 0; y < kRows; ++y) {
+                        const T v = vu[32 * y];
+#pragma unroll
+                        for (int x = 0; x < kCols; ++x) acc[y][x] -= v * wv[x][u];
+                    }
+                }
+#pragma unroll
+                for (int y = 0; y < kRows; ++y)
+#pragma unroll
+                    for (int x = 0; x < kCols; ++x)
+                        if (has[x]) tc[x][r + 32 * y] = acc[y][x];
+                continue;
+            }
 #pragma unroll
             for (int y = 0; y < kRows; ++y)
 #pragma unroll

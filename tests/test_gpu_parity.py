@@ -152,6 +152,56 @@ def test_powerlaw_all_bins(precision):
         check_fp32_every_column(P, res, rho, ref)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_powerlaw_large_columns_sampled(precision):
+    """The global bin's largest columns: |I| beyond what one 16-column FP32 panel
+    can stage (so panels factored on fewer rows are applied later one reflector
+    at a time, and the refinement reads a panel's reflectors from the slab),
+    with the QR update, drops and refactorizations.  The 8 columns with the
+    largest |I| and 4 random ones of an n = 12000 power law against the oracle
+    built on those columns."""
+    import os
+    import scipy.sparse as sp
+
+    P = gen.powerlaw(12000, seed=23)
+    kw = dict(c=5, l_max=8, eps=0.4, tol=1e-3, drop="fixed")
+    h, dA, res, rho, loops, flags, st = gpu_M(P, precision=precision, **kw)
+    assert st["n_failed"] == 0 and st["cols_bin"][2] > 0
+    staged_rows = (227 * 1024 - 2048) // 4 // 16  # rows of a 16-column FP32 panel in the staging area
+    assert st["q_max"] > staged_rows
+    cp, rows, vals = csc_from_csr(*res, P.n)
+    # |I_k| from the GPU's pattern: the nonzero rows of |A| |M|(:,k)
+    Ab = sp.csr_matrix((np.ones(P.nnz), P.col_idx, P.row_ptr), shape=(P.n, P.n))
+    Mb = sp.csc_matrix((np.ones(len(rows)), rows, cp), shape=(P.n, P.n))
+    qk = np.diff((Ab @ Mb).tocsc().indptr)
+    rng = np.random.default_rng(5)
+    big = np.argsort(-qk, kind="stable")[:8]
+    pick = np.unique(np.concatenate([big, rng.choice(P.n, 4, replace=False)]))
+    assert qk[big[0]] > staged_rows
+    ref = oracle.build(P, cols=pick, threads=os.cpu_count() or 1, **kw)
+    for t, k in enumerate(pick):
+        Jo, vo = ref.column(t)
+        Jg, vg = rows[cp[k]:cp[k + 1]], vals[cp[k]:cp[k + 1]]
+        if precision == "fp64":
+            assert np.array_equal(Jg, Jo), k
+            np.testing.assert_allclose(vg, vo, rtol=1e-9, atol=1e-15 * np.abs(vo).max())
+            assert rho[k] == pytest.approx(ref.rho[t], rel=1e-9, abs=1e-14)
+            assert loops[k] == ref.loops[t]
+        elif np.array_equal(Jg, Jo):
+            assert rho[k] == pytest.approx(ref.rho[t], rel=1e-5, abs=1e-12)
+    if precision != "fp64":
+        # every sampled column: ||r_k|| against the FP64 solution on the GPU's own pattern
+        sub = np.zeros(P.n + 1, np.int64)
+        lens = np.zeros(P.n, np.int64)
+        lens[pick] = np.diff(cp)[pick]
+        sub[1:] = np.cumsum(lens)
+        srows = np.concatenate([rows[cp[k]:cp[k + 1]] for k in pick]).astype(np.int32)
+        ov, orho2 = oracle.refit(P, sub, srows, threads=os.cpu_count() or 1)
+        np.testing.assert_allclose(rho[pick], np.sqrt(orho2[pick]), rtol=1e-5, atol=1e-12)
+        sv = np.concatenate([vals[cp[k]:cp[k + 1]] for k in pick])
+        np.testing.assert_allclose(sv, ov, rtol=1e-6, atol=1e-6 * np.abs(ov).max())
+
+
 def test_rebuild_graph_is_identical(c1):
     dA = rsai.DeviceMatrix.from_host(c1)
     h = rsai.build(dA, drop="fixed", precision="fp64", **PARAMS_C1)
