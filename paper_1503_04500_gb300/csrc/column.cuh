@@ -470,8 +470,9 @@ template <typename T> __device__ __forceinline__ T warp_reduce_scatter16(T (&v)[
 }
 
 // out[0..kPanel) = the sums of v[0..kPanel) over the CTA, visible to every
-// thread on return (two synchronisations; the warps' partial sums go through
-// red, kPanel per warp, and are added in warp order).
+// thread on return (two synchronisations).  The warps' partial sums go through
+// red, kPanel per warp; warp 0 adds them, lane l taking entry l % kPanel over
+// every other warp and one shuffle joining the two halves.
 template <class Team, typename T>
 __device__ __forceinline__ void team_sum16(const Team &team, T (&v)[kPanel], T *red, T *out) {
     constexpr int NW = Team::SIZE / 32;
@@ -479,11 +480,13 @@ __device__ __forceinline__ void team_sum16(const Team &team, T (&v)[kPanel], T *
     const T sv = warp_reduce_scatter16(v, lane);
     if ((lane & 1) == 0) red[(me >> 5) * kPanel + rs_entry(lane)] = sv;
     team.sync();
-    if (me < kPanel) {
-        T a = red[me];
+    if (me < 32) {
+        const int e = lane & (kPanel - 1);
+        T a = T(0);
 #pragma unroll
-        for (int w = 1; w < NW; ++w) a += red[w * kPanel + me];
-        out[me] = a;
+        for (int w = lane >> 4; w < NW; w += 2) a += red[w * kPanel + e];
+        a += __shfl_xor_sync(0xffffffffu, a, 16);
+        if (lane < kPanel) out[lane] = a;
     }
     team.sync();
 }
@@ -551,13 +554,14 @@ __device__ void back_substitute_blocked(const Team &team, const T *B, int q, int
 }
 
 // Householder QR of the staged panel V (rows 0..qq-1, nb <= kPanel columns,
-// ld qq, shared memory) with the T of its compact-WY form built alongside.
-// Step t makes one pass over rows r >= t for x.x (x = column t), c.x for the
-// trailing panel columns c and v_s.x for the earlier reflectors s, and one
-// CTA reduction of the kPanel sums.  Since v_t differs from x only in its head
-// (v0 instead of x0), v_t.c = c.x + (v0 - x0) c_t and Y(s,t) = v_s.v_t =
-// v_s.x + (v0 - x0) v_s(t); then T(t,t) = tau_t and
-// T(s,t) = -tau_t sum_{s <= s2 < t} T(s,s2) Y(s2,t) (tm[s * kPanel + t]).
+// ld qq, shared memory) with the T of its compact-WY form.  Step t makes one
+// pass over rows r >= t for x.x (x = column t), c.x for the trailing panel
+// columns c and v_s.x for the earlier reflectors s, and one CTA reduction of
+// the kPanel sums.  Since v_t differs from x only in its head (v0 instead of
+// x0), v_t.c = c.x + (v0 - x0) c_t and Y(s,t) = v_s.v_t = v_s.x + (v0 - x0) v_s(t).
+// Y(s,t) is kept below the diagonal of tm (tm[t * kPanel + s]) and tau_t on it;
+// after the last step one warp forms T(t,t) = tau_t and
+// T(s,t) = -tau_t sum_{s <= s2 < t} T(s,s2) Y(s2,t) above it (tm[s * kPanel + t]).
 // Leaves R on and above the diagonal, the reflector tails below it, and
 // vhead[t] = v0, taus[t] = 2 / v^T v.
 template <class Team, typename T>
@@ -583,9 +587,14 @@ __device__ __forceinline__ void panel_factor_fused(const Team &team, T *V, int q
         const T v0 = x0 - alpha;
         const T vtv = sigma - x0 * x0 + v0 * v0;
         const T two_over = (vtv > T(0)) ? T(2) / vtv : T(0);
-        if (me < nb && me != t) {
-            const T d = out[me] + (v0 - x0) * V[(int64_t)me * qq + t];
-            out2[me] = (me > t) ? d * two_over : d;  // f_c for c > t, Y(s,t) for s < t
+        if (me < nb) {
+            if (me == t) {
+                tm[t * kPanel + t] = two_over;
+            } else {
+                const T d = out[me] + (v0 - x0) * V[(int64_t)me * qq + t];
+                if (me > t) out2[me] = d * two_over;  // f_c for the trailing column c = me
+                else tm[t * kPanel + me] = d;          // Y(s,t) for the earlier reflector s = me
+            }
         }
         team.sync();
         if (two_over > T(0)) {
@@ -596,13 +605,6 @@ __device__ __forceinline__ void panel_factor_fused(const Team &team, T *V, int q
                     if (u > t && u < nb) V[(int64_t)u * qq + r] -= out2[u] * vr;
             }
         }
-        if (me < t) {
-            T a = 0;
-            for (int s2 = me; s2 < t; ++s2) a += tm[me * kPanel + s2] * out2[s2];
-            tm[me * kPanel + t] = -two_over * a;
-        } else if (me == t) {
-            tm[t * kPanel + t] = two_over;
-        }
         team.sync();
         if (me == 0) {
             x[t] = alpha;
@@ -610,6 +612,29 @@ __device__ __forceinline__ void panel_factor_fused(const Team &team, T *V, int q
             taus[t] = two_over;
         }
         rank_flag |= (fabs(alpha) <= small) ? 1 : 0;
+    }
+    // T from Y and tau: lane s of warp 0 holds row s of T
+    if (me < 32) {
+        const int sr = me;
+        T trow[kPanel];
+#pragma unroll
+        for (int t = 0; t < kPanel; ++t) {
+            trow[t] = T(0);
+            if (t < nb) {
+                const T tau = tm[t * kPanel + t];
+                T a = T(0);
+#pragma unroll
+                for (int s2 = 0; s2 < t; ++s2)
+                    if (s2 >= sr) a += trow[s2] * tm[t * kPanel + s2];
+                if (sr < t) trow[t] = -tau * a;
+                else if (sr == t) trow[t] = tau;
+            }
+        }
+        if (sr < nb) {
+#pragma unroll
+            for (int t = 0; t < kPanel; ++t)
+                if (t > sr && t < nb) tm[sr * kPanel + t] = trow[t];
+        }
     }
     team.sync();
 }
@@ -646,16 +671,23 @@ __device__ __noinline__ void apply_qt_panels(Team team, const T *B, int q, int p
         T acc[kPanel];
 #pragma unroll
         for (int u = 0; u < kPanel; ++u) acc[u] = T(0);
-        for (int i = j0 + me; i < q; i += Team::SIZE) {
-            const T x = rhs[i];
-            const int r = i - j0;
+        if (staged) {
+            for (int r = me; r < qq; r += Team::SIZE) {
+                const T x = rhs[j0 + r];
 #pragma unroll
-            for (int u = 0; u < kPanel; ++u) {
-                if (u < nb) {
-                    const int j = j0 + u;
-                    const T v = staged ? V[(int64_t)u * qq + r]
-                                       : ((i > j) ? B[(int64_t)j * q + i] : ((i == j) ? vhead[j] : T(0)));
-                    acc[u] += v * x;
+                for (int u = 0; u < kPanel; ++u)
+                    if (u < nb) acc[u] += V[(int64_t)u * qq + r] * x;
+            }
+        } else {
+            for (int i = j0 + me; i < q; i += Team::SIZE) {
+                const T x = rhs[i];
+#pragma unroll
+                for (int u = 0; u < kPanel; ++u) {
+                    if (u < nb) {
+                        const int j = j0 + u;
+                        const T v = (i > j) ? B[(int64_t)j * q + i] : ((i == j) ? vhead[j] : T(0));
+                        acc[u] += v * x;
+                    }
                 }
             }
         }
@@ -666,19 +698,27 @@ __device__ __noinline__ void apply_qt_panels(Team team, const T *B, int q, int p
             out2[me] = y;
         }
         team.sync();
-        for (int i = j0 + me; i < q; i += Team::SIZE) {
-            T a = rhs[i];
-            const int r = i - j0;
+        if (staged) {
+            for (int r = me; r < qq; r += Team::SIZE) {
+                T a = rhs[j0 + r];
 #pragma unroll
-            for (int u = 0; u < kPanel; ++u) {
-                if (u < nb) {
-                    const int j = j0 + u;
-                    const T v = staged ? V[(int64_t)u * qq + r]
-                                       : ((i > j) ? B[(int64_t)j * q + i] : ((i == j) ? vhead[j] : T(0)));
-                    a -= v * out2[u];
-                }
+                for (int u = 0; u < kPanel; ++u)
+                    if (u < nb) a -= V[(int64_t)u * qq + r] * out2[u];
+                rhs[j0 + r] = a;
             }
-            rhs[i] = a;
+        } else {
+            for (int i = j0 + me; i < q; i += Team::SIZE) {
+                T a = rhs[i];
+#pragma unroll
+                for (int u = 0; u < kPanel; ++u) {
+                    if (u < nb) {
+                        const int j = j0 + u;
+                        const T v = (i > j) ? B[(int64_t)j * q + i] : ((i == j) ? vhead[j] : T(0));
+                        a -= v * out2[u];
+                    }
+                }
+                rhs[i] = a;
+            }
         }
         team.sync();
         j0 += nb;
