@@ -573,7 +573,19 @@ __device__ __forceinline__ void panel_factor_fused(const Team &team, T *V, int q
         T acc[kPanel];
 #pragma unroll
         for (int u = 0; u < kPanel; ++u) acc[u] = T(0);
-        for (int r = t + me; r < qq; r += Team::SIZE) {
+        // two rows per thread and iteration: their loads are issued together
+        int r = t + me;
+        for (; r + Team::SIZE < qq; r += 2 * Team::SIZE) {
+            const T xa = x[r], xb = x[r + Team::SIZE];
+#pragma unroll
+            for (int u = 0; u < kPanel; ++u) {
+                if (u < nb) {
+                    const T *vu = V + (int64_t)u * qq + r;
+                    acc[u] += vu[0] * xa + vu[Team::SIZE] * xb;
+                }
+            }
+        }
+        if (r < qq) {
             const T xr = x[r];
 #pragma unroll
             for (int u = 0; u < kPanel; ++u)
@@ -598,11 +610,25 @@ __device__ __forceinline__ void panel_factor_fused(const Team &team, T *V, int q
         }
         team.sync();
         if (two_over > T(0)) {
-            for (int r = t + me; r < qq; r += Team::SIZE) {
-                const T vr = (r == t) ? v0 : x[r];
+            int r2 = t + me;
+            for (; r2 + Team::SIZE < qq; r2 += 2 * Team::SIZE) {
+                const T va = (r2 == t) ? v0 : x[r2], vb = x[r2 + Team::SIZE];
+#pragma unroll
+                for (int u = 0; u < kPanel; ++u) {
+                    if (u > t && u < nb) {
+                        T *cu = V + (int64_t)u * qq + r2;
+                        const T f = out2[u];
+                        const T ca = cu[0], cb = cu[Team::SIZE];
+                        cu[0] = ca - f * va;
+                        cu[Team::SIZE] = cb - f * vb;
+                    }
+                }
+            }
+            if (r2 < qq) {
+                const T vr = (r2 == t) ? v0 : x[r2];
 #pragma unroll
                 for (int u = 0; u < kPanel; ++u)
-                    if (u > t && u < nb) V[(int64_t)u * qq + r] -= out2[u] * vr;
+                    if (u > t && u < nb) V[(int64_t)u * qq + r2] -= out2[u] * vr;
             }
         }
         team.sync();
@@ -1222,7 +1248,8 @@ template <class Team, typename T> struct Column {
     }
 
     // S = I u {k}; r = A(:,J) m - e_k on S in double (Eq. 2.4), row by row
-    // through the CSR of A (ascending j, so the sum order is fixed).
+    // through the CSR of A: in ascending j on the warp bins (the oracle's
+    // order), a fixed lane-strided order and butterfly on the CTA bins.
     // `refine`: the residual of a refinement step (counted as refinement work).
     __device__ void residual(bool refine = false) {
         const int me = team.rank();
@@ -1235,30 +1262,61 @@ template <class Team, typename T> struct Column {
             else row = (i < pk) ? w.I[i] : (i == pk ? k : w.I[i - 1]);
             w.S[i] = row;
         }
-        team.sync();
         double ss = 0.0;
         int cnt = 0;
-        for (int i = me; i < s; i += Team::SIZE) {
-            const int32_t row = w.S[i];
-            const int64_t e0 = A.row_ptr[row], e1 = A.row_ptr[row + 1];
-            double acc = 0.0;
-            for (int64_t e = e0; e < e1; e += kRowGroup) {
-                int32_t cj[kRowGroup];
-                double av[kRowGroup];
-#pragma unroll
-                for (int u = 0; u < kRowGroup; ++u) {
-                    cj[u] = (e + u < e1) ? A.col_idx[e + u] : -1;
-                    av[u] = (e + u < e1) ? A.val[e + u] : 0.0;
+        if constexpr (!is_lane_team<Team>::value) {
+            // CTA teams: a warp per row, its lanes over the row's entries (rows of
+            // I can hold hundreds), summed by a fixed butterfly.  The global-memory
+            // bins search a copy of J in the staging area (shared memory).
+            const int32_t *Js = w.J;
+            if (cap.stage_bytes > 0 && (size_t)p * sizeof(int32_t) <= (size_t)cap.stage_bytes) {
+                int32_t *jc = reinterpret_cast<int32_t *>(w.stage);
+                for (int c = me; c < p; c += Team::SIZE) jc[c] = w.J[c];
+                Js = jc;
+            }
+            team.sync();
+            const int lane = me & 31;
+            constexpr int NWR = Team::SIZE / 32;
+            for (int i = me >> 5; i < s; i += NWR) {
+                const int32_t row = w.S[i];
+                const int64_t e0 = A.row_ptr[row], e1 = A.row_ptr[row + 1];
+                double acc = 0.0;
+                for (int64_t e = e0 + lane; e < e1; e += 32) {
+                    const int pos = find_i32(Js, p, A.col_idx[e]);
+                    if (pos >= 0) { acc = fma(A.val[e], w.m[pos], acc); ++cnt; }
                 }
 #pragma unroll
-                for (int u = 0; u < kRowGroup; ++u) {
-                    int pos = (cj[u] >= 0) ? find_J(cj[u]) : -1;
-                    if (pos >= 0) { acc = fma(av[u], w.m[pos], acc); ++cnt; }
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (row == k) acc -= 1.0;
+                if (lane == 0) {
+                    w.r[i] = acc;
+                    if (!refine) ss = fma(acc, acc, ss);
                 }
             }
-            if (row == k) acc -= 1.0;
-            w.r[i] = acc;
-            if (!refine) ss = fma(acc, acc, ss);
+        } else {
+            team.sync();
+            for (int i = me; i < s; i += Team::SIZE) {
+                const int32_t row = w.S[i];
+                const int64_t e0 = A.row_ptr[row], e1 = A.row_ptr[row + 1];
+                double acc = 0.0;
+                for (int64_t e = e0; e < e1; e += kRowGroup) {
+                    int32_t cj[kRowGroup];
+                    double av[kRowGroup];
+#pragma unroll
+                    for (int u = 0; u < kRowGroup; ++u) {
+                        cj[u] = (e + u < e1) ? A.col_idx[e + u] : -1;
+                        av[u] = (e + u < e1) ? A.val[e + u] : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kRowGroup; ++u) {
+                        int pos = (cj[u] >= 0) ? find_J(cj[u]) : -1;
+                        if (pos >= 0) { acc = fma(av[u], w.m[pos], acc); ++cnt; }
+                    }
+                }
+                if (row == k) acc -= 1.0;
+                w.r[i] = acc;
+                if (!refine) ss = fma(acc, acc, ss);
+            }
         }
         // the refinement step reads r only; its norm is not formed
         if (!refine) rho = sqrt(team.sum(ss));
