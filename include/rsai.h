@@ -304,13 +304,14 @@ rsai_status rsai_build_phase_times(rsai_handle *h, void *stream, double *ms);
  *       with rsai_get_M) or NULL;  b, x : device arrays of length n.
  * It allocates nothing: its work vectors live in one fixed device array inside
  * the library (about 4.7 MB, held by every GPU that loads the library until the
- * process exits) and n must not exceed 65536 (else RSAI_ERR_TOO_LARGE).  The
- * first call on each device looks up the array's device address (and keeps it),
- * so make that first call before any stream capture begins; after a
+ * process exits) and n must not exceed 65536 (else RSAI_ERR_TOO_LARGE).  Like
+ * rsai_bicgstab it waits for the stream at every iteration to read the scalars
+ * of its stopping test, so it cannot be captured into a CUDA graph.  The first
+ * call on each device looks up the array's device address (and keeps it); make
+ * that first call while no stream of the process is being captured.  After a
  * cudaDeviceReset of a device the kept address is stale, so do not call it on
- * that device again.  Like rsai_bicgstab it waits for the stream at every
- * iteration to read the scalars of its stopping test.  Every call shares the
- * array: calls that overlap on the GPU race and must be ordered on one stream.
+ * that device again.  Every call shares the array: calls that overlap on the
+ * GPU race and must be ordered on one stream.
  * It runs rsai_bicgstab's solver code: same results, statuses and outputs.
  */
 rsai_status rsai_bicgstab_noalloc(const rsai_csr *A, const rsai_csr *M, const double *b, double *x, double rtol,

@@ -24,10 +24,11 @@
 //
 // Set-up: the first call on each device (with that device current) looks up
 // the array's device address with cudaGetSymbolAddress and keeps it for the
-// later calls on that device; make that first call before any stream capture
-// begins.  A cudaDeviceReset unloads the library's device code, and the kept
-// address is then stale: do not call this entry point on a device after
-// resetting it.
+// later calls on that device; make that first call while no stream of the
+// process is being captured.  The solve itself waits for the stream at every
+// iteration, so it never runs inside a capture.  A cudaDeviceReset unloads the
+// library's device code, and the kept address is then stale: do not call this
+// entry point on a device after resetting it.
 #include <mutex>
 
 #include "kernels.h"
