@@ -678,76 +678,85 @@ __device__ __noinline__ void apply_qt_panels(Team team, const T *B, int q, int p
     T *red = stage + kPanel * kPanel, *out = red + NW * kPanel, *out2 = out + kPanel;
     T *V = stage + kStageHead<Team>;
     const int64_t velems = (int64_t)stage_bytes / (int64_t)sizeof(T) - kStageHead<Team>;
-    for (int j0 = 0; j0 < p;) {
-        const int nb = pnb[j0];
-        const int qq = q - j0;
-        const bool staged = nb > 1 && (int64_t)nb * qq <= velems;
-        if (staged) {
-            for (int t = 0; t < nb; ++t) {
-                const T *src = B + (int64_t)(j0 + t) * q + j0;
-                T *dst = V + (int64_t)t * qq;
+    for (int jp = 0; jp < p;) {
+        const int nbp = pnb[jp];
+        // sub-panels of as many reflectors as the staging area holds (the
+        // diagonal blocks of a panel's T are the T's of its sub-panels); a
+        // sub-panel that cannot be staged reads its reflectors from the slab
+        for (int js = 0; js < nbp;) {
+            const int j0 = jp + js;
+            const int qq = q - j0;
+            const int64_t fit = velems / (int64_t)max(qq, 1);
+            const bool staged = nbp - js > 1 && fit >= 2;
+            const int nb = staged ? (int)min((int64_t)(nbp - js), fit) : nbp - js;
+            if (staged) {
+                for (int t = 0; t < nb; ++t) {
+                    const T *src = B + (int64_t)(j0 + t) * q + j0;
+                    T *dst = V + (int64_t)t * qq;
+                    for (int r = me; r < qq; r += Team::SIZE) {
+                        if (r > t) cp_async_elem(dst + r, src + r);
+                        else dst[r] = (r == t) ? vhead[j0 + t] : T(0);
+                    }
+                }
+                cp_async_wait();
+                team.sync();
+            }
+            T acc[kPanel];
+#pragma unroll
+            for (int u = 0; u < kPanel; ++u) acc[u] = T(0);
+            if (staged) {
                 for (int r = me; r < qq; r += Team::SIZE) {
-                    if (r > t) cp_async_elem(dst + r, src + r);
-                    else dst[r] = (r == t) ? vhead[j0 + t] : T(0);
+                    const T x = rhs[j0 + r];
+#pragma unroll
+                    for (int u = 0; u < kPanel; ++u)
+                        if (u < nb) acc[u] += V[(int64_t)u * qq + r] * x;
+                }
+            } else {
+                for (int i = j0 + me; i < q; i += Team::SIZE) {
+                    const T x = rhs[i];
+#pragma unroll
+                    for (int u = 0; u < kPanel; ++u) {
+                        if (u < nb) {
+                            const int j = j0 + u;
+                            const T v = (i > j) ? B[(int64_t)j * q + i] : ((i == j) ? vhead[j] : T(0));
+                            acc[u] += v * x;
+                        }
+                    }
                 }
             }
-            cp_async_wait();
+            team_sum16(team, acc, red, out);
+            if (me < nb) {
+                T y = 0;
+                for (int s2 = 0; s2 <= me; ++s2) y += Tst[(int64_t)(j0 + me) * kPanel + js + s2] * out[s2];
+                out2[me] = y;
+            }
             team.sync();
-        }
-        T acc[kPanel];
+            if (staged) {
+                for (int r = me; r < qq; r += Team::SIZE) {
+                    T a = rhs[j0 + r];
 #pragma unroll
-        for (int u = 0; u < kPanel; ++u) acc[u] = T(0);
-        if (staged) {
-            for (int r = me; r < qq; r += Team::SIZE) {
-                const T x = rhs[j0 + r];
+                    for (int u = 0; u < kPanel; ++u)
+                        if (u < nb) a -= V[(int64_t)u * qq + r] * out2[u];
+                    rhs[j0 + r] = a;
+                }
+            } else {
+                for (int i = j0 + me; i < q; i += Team::SIZE) {
+                    T a = rhs[i];
 #pragma unroll
-                for (int u = 0; u < kPanel; ++u)
-                    if (u < nb) acc[u] += V[(int64_t)u * qq + r] * x;
-            }
-        } else {
-            for (int i = j0 + me; i < q; i += Team::SIZE) {
-                const T x = rhs[i];
-#pragma unroll
-                for (int u = 0; u < kPanel; ++u) {
-                    if (u < nb) {
-                        const int j = j0 + u;
-                        const T v = (i > j) ? B[(int64_t)j * q + i] : ((i == j) ? vhead[j] : T(0));
-                        acc[u] += v * x;
+                    for (int u = 0; u < kPanel; ++u) {
+                        if (u < nb) {
+                            const int j = j0 + u;
+                            const T v = (i > j) ? B[(int64_t)j * q + i] : ((i == j) ? vhead[j] : T(0));
+                            a -= v * out2[u];
+                        }
                     }
+                    rhs[i] = a;
                 }
             }
+            team.sync();
+            js += nb;
         }
-        team_sum16(team, acc, red, out);
-        if (me < nb) {
-            T y = 0;
-            for (int s2 = 0; s2 <= me; ++s2) y += Tst[(int64_t)(j0 + me) * kPanel + s2] * out[s2];
-            out2[me] = y;
-        }
-        team.sync();
-        if (staged) {
-            for (int r = me; r < qq; r += Team::SIZE) {
-                T a = rhs[j0 + r];
-#pragma unroll
-                for (int u = 0; u < kPanel; ++u)
-                    if (u < nb) a -= V[(int64_t)u * qq + r] * out2[u];
-                rhs[j0 + r] = a;
-            }
-        } else {
-            for (int i = j0 + me; i < q; i += Team::SIZE) {
-                T a = rhs[i];
-#pragma unroll
-                for (int u = 0; u < kPanel; ++u) {
-                    if (u < nb) {
-                        const int j = j0 + u;
-                        const T v = (i > j) ? B[(int64_t)j * q + i] : ((i == j) ? vhead[j] : T(0));
-                        a -= v * out2[u];
-                    }
-                }
-                rhs[i] = a;
-            }
-        }
-        team.sync();
-        j0 += nb;
+        jp += nbp;
     }
 }
 
@@ -852,9 +861,10 @@ __device__ __noinline__ void apply_qt_team(Team team, const T *B, int q, int p, 
 // finished factor (built on q0 rows; every row below is zero in them) applied
 // to the appended columns p0..p-1 of B (ld q), rows j..q0-1.  In the
 // global-memory bins (pnb != nullptr) the reflectors go panel by panel as
-// they were factored: a panel whose explicit V fits the staging area is
-// applied in compact-WY form with its stored T.  Otherwise (and in the
-// shared-memory bins) one reflector per pass, one warp per column.
+// they were factored, each panel in compact-WY form with its stored T, split
+// into sub-panels when its explicit V outgrows the staging area (q has grown
+// since it was factored).  Sub-panels of fewer than four reflectors, and the
+// shared-memory bins, take one reflector per pass, one warp per column.
 template <class Team, typename T>
 __device__ __noinline__ void qr_update_apply(Team team, T *B, int q, int p, int q0, int p0, const T *vhead,
                                              const T *taus, T *stage, int stage_bytes, const T *Tst,
@@ -867,43 +877,47 @@ __device__ __noinline__ void qr_update_apply(Team team, T *B, int q, int p, int 
     const int64_t velems = stage_bytes > 0 ? (int64_t)stage_bytes / (int64_t)sizeof(T) - kStageHead<Team> : 0;
     int j0 = 0;
     while (j0 < p0) {
-        const int qq = q0 - j0;
         const int nb = pnb ? pnb[j0] : 1;
-        if (nb < 4 || (int64_t)nb * qq > velems) {
-            for (int j = j0; j < j0 + nb; ++j) {
-                const T *col = B + (int64_t)j * q;
-                const T v0 = vhead[j], two_over = taus[j];
+        // the panel in sub-panels of as many reflectors as the staging area holds:
+        // the diagonal blocks of a panel's T are the T's of its sub-panels
+        for (int js = 0; js < nb;) {
+            const int j1 = j0 + js, qq = q0 - j1;
+            const int ns = (int)min((int64_t)(nb - js), qq > 0 ? velems / (int64_t)qq : (int64_t)0);
+            if (ns < 4) {  // one reflector, one warp per column
+                const T *col = B + (int64_t)j1 * q;
+                const T v0 = vhead[j1], two_over = taus[j1];
                 if (two_over > T(0)) {
                     for (int c = p0 + wid; c < p; c += NW) {
                         T *t = B + (int64_t)c * q;
                         T d = 0;
-                        for (int i = j + lane; i < q0; i += 32) d += ((i == j) ? v0 : col[i]) * t[i];
+                        for (int i = j1 + lane; i < q0; i += 32) d += ((i == j1) ? v0 : col[i]) * t[i];
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
                         const T f = d * two_over;
-                        for (int i = j + lane; i < q0; i += 32) t[i] -= f * ((i == j) ? v0 : col[i]);
+                        for (int i = j1 + lane; i < q0; i += 32) t[i] -= f * ((i == j1) ? v0 : col[i]);
                     }
                 }
                 team.sync();
+                ++js;
+                continue;
             }
-            j0 += nb;
-            continue;
-        }
-        for (int t = 0; t < nb; ++t) {
-            const T *src = B + (int64_t)(j0 + t) * q + j0;
-            T *dst = V + (int64_t)t * qq;
-            for (int r = me; r < qq; r += Team::SIZE) {
-                if (r > t) cp_async_elem(dst + r, src + r);
-                else dst[r] = (r == t) ? vhead[j0 + t] : T(0);
+            for (int t = 0; t < ns; ++t) {
+                const T *src = B + (int64_t)(j1 + t) * q + j1;
+                T *dst = V + (int64_t)t * qq;
+                for (int r = me; r < qq; r += Team::SIZE) {
+                    if (r > t) cp_async_elem(dst + r, src + r);
+                    else dst[r] = (r == t) ? vhead[j1 + t] : T(0);
+                }
             }
+            cp_async_wait();
+            for (int e = me; e < kPanel * kPanel; e += Team::SIZE) {
+                const int s2 = e / kPanel, t = e - s2 * kPanel;
+                tm[e] = (t < ns && s2 <= t) ? Tst[(int64_t)(j1 + t) * kPanel + js + s2] : T(0);
+            }
+            team.sync();
+            wy_apply(team, V, qq, ns, tm, B, q, p, (T *)nullptr, j1, p0, p - 1);
+            js += ns;
         }
-        cp_async_wait();
-        for (int e = me; e < kPanel * kPanel; e += Team::SIZE) {
-            const int s2 = e / kPanel, t = e - s2 * kPanel;
-            tm[e] = (t < nb && s2 <= t) ? Tst[(int64_t)(j0 + t) * kPanel + s2] : T(0);
-        }
-        team.sync();
-        wy_apply(team, V, qq, nb, tm, B, q, p, (T *)nullptr, j0, p0, p - 1);
         j0 += nb;
     }
 }
