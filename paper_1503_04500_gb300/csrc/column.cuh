@@ -268,7 +268,9 @@ __device__ __noinline__ int qr_factor_team(Team team, T *B, int q, int p, T *rhs
 
 // Compact-WY pieces shared by the panel factorization and the QR update.
 // V: nb explicit reflectors (zeros above the diagonal, heads on it) of
-// length qq in shared memory, ld qq; taus: their 2 / v^T v.
+// length qq in shared memory, ld qq; taus: their 2 / v^T v.  wy_form_T forms
+// T from V alone; the staged factorization forms it alongside instead
+// (panel_factor_fused), so wy_form_T has no caller at present.
 // T (kPanel x kPanel in tm) of H_0 ... H_{nb-1} = I - V T V^T:
 // y(s,t) = v_s^T v_t (s < t), then column by column
 // T(t,t) = tau_t, T(0:t, t) = -tau_t T(0:t, 0:t) y(0:t, t).
@@ -763,17 +765,19 @@ __device__ __noinline__ void apply_qt_panels(Team team, const T *B, int q, int p
 // Blocked Householder QR (compact WY) for the bins whose workspace is in
 // global memory.  Panels of nb <= kPanel columns (nb chosen so that rows j0..q
 // of the panel fit the shared-memory staging area) are copied to shared
-// memory, factored there, written back, and turned into explicit reflectors V
-// (zeros above the head, v(j) on the diagonal); with T upper triangular,
-// H_1...H_nb = I - V T V^T, every trailing column and the right-hand side get
+// memory (cp.async), factored there with their T (panel_factor_fused), written
+// back, and turned into explicit reflectors V (zeros above the head, v(j) on
+// the diagonal); with T upper triangular, H_1...H_nb = I - V T V^T, every
+// trailing column and the right-hand side get
 //   C <- C - V (T^T (V^T C))
 // in one pass (one warp per four columns), so the trailing matrix in global memory
-// is streamed once per panel instead of once per reflector.  A panel that does
-// not fit four columns falls back to single Householder steps.  The
-// reflectors, R and rhs are those of the unblocked version up to rounding.
-// j_start > 0 factors only columns j_start..p-1 (the columns appended to a
-// factor whose first j_start columns are done, Section 3); backsub = false
-// leaves Q^T rhs in rhs.
+// is streamed once per panel instead of once per reflector.  Each panel's size
+// and T are kept (pnb, Tst) for the QR update and the refinement.  A panel that
+// does not fit four columns falls back to single Householder steps (panels of
+// one).  The reflectors, R and rhs are those of the unblocked version up to
+// rounding.  j_start > 0 factors only columns j_start..p-1 (the columns
+// appended to a factor whose first j_start columns are done, Section 3);
+// backsub = false leaves Q^T rhs in rhs.
 template <class Team, typename T>
 __device__ __noinline__ int qr_solve_staged(Team team, T *B, int q, int p, T *rhs, T *vhead, T *taus, T small,
                                             T *stage, int stage_bytes, T *Tst, int32_t *pnb,
