@@ -672,8 +672,9 @@ __device__ __forceinline__ void panel_factor_fused(const Team &team, T *V, int q
 // rhs <- rhs - V y, with V = the explicit reflectors (vhead on the diagonal,
 // the tails of B below it).  A panel is taken in sub-panels of as many
 // reflectors as the staging area holds (the diagonal blocks of its T); each is
-// copied there first (cp.async) and both passes read shared memory.  A single
-// reflector that does not fit reads its tail from the slab.
+// copied there first (cp.async) and both passes read shared memory.  When
+// fewer than two reflectors fit, or one is left, the rest of the panel reads
+// its tails from the slab.
 template <class Team, typename T>
 __device__ __noinline__ void apply_qt_panels(Team team, const T *B, int q, int p, T *rhs, const T *vhead,
                                              const T *Tst, const int32_t *pnb, T *stage, int stage_bytes) {
